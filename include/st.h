@@ -1,0 +1,160 @@
+/*
+ * st.h -- C ABI of the GB300 spherical-harmonic spectral transform.
+ *
+ * The transform is the one stated in ESCAPE D3.3 (arXiv 1908.06096),
+ * section 4.4.1 (and again in 4.4.2): the synthesis
+ *
+ *     f(theta, lambda) = sum_{m=-T}^{T} e^{i m lambda}
+ *                          sum_{n=|m|}^{T} a_n^m Pbar_n^m(cos theta)
+ *
+ * ("inverse", spectral -> grid) and its inverse ("direct", grid -> spectral),
+ * where each coefficient is the projection of the field on one basis
+ * function (section 4.4.2), evaluated with Gaussian quadrature in latitude.
+ * Both run as the two stages of section 4.4.1's figure: FFTs along each
+ * latitude row and a Legendre transform along latitude, which section 4.2.4
+ * carries out as matrix multiplications, one per zonal wavenumber m.
+ *
+ * Conventions (the paper leaves these open; the readings are fixed here):
+ *  - theta is colatitude; mu = cos(theta).  Gaussian latitudes run north to
+ *    south.  Pbar_n^m is normalised to unit L2 norm on [-1, 1], without the
+ *    Condon-Shortley phase.  Truncation is triangular at T.
+ *  - Spectral array, per field: m-major triangular, complex interleaved
+ *    (re, im); coefficient (m, n), 0 <= m <= n <= T, sits at complex index
+ *    m (T+1) - m (m-1)/2 + (n - m).  Fields are stored one after another.
+ *    Only m >= 0 is stored (a_n^{-m} = conj(a_n^m)); Im a_n^0 is ignored on
+ *    input and written as 0 on output.
+ *  - Grid array, per field: rows north to south, concatenated; row j holds
+ *    N_j points at longitudes 2 pi k / N_j.  Fields one after another.
+ *  - A row keeps wavenumbers m <= M_j = min(T, floor((N_j - 1) / 2)).
+ *  - Element type: double for ST_FP64 plans, float for every other
+ *    precision.  All pointers passed to the transforms are DEVICE pointers
+ *    unless a name says _host.
+ *
+ * Ownership: the caller owns every input and output buffer.  A plan owns its
+ * Gaussian nodes, Legendre tables, FFT row data and workspace; all are freed
+ * by st_plan_destroy.
+ *
+ * Asynchrony: st_inv_trans / st_dir_trans enqueue work on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and return without waiting.
+ * Argument and launch errors are returned at once.  A device-side error (a
+ * bounded wait that gave up inside a kernel) is recorded in the plan and
+ * returned by the next st_plan_sync.
+ *
+ * Concurrency: one plan runs one transform at a time (its workspace is
+ * shared by both directions).  Calls on one plan must be ordered on one
+ * stream; use one plan per stream for concurrent transforms.
+ */
+#ifndef ST_H
+#define ST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct st_plan *st_plan_t;
+
+typedef enum {
+    ST_OK = 0,
+    ST_ERR_ARG = 1,         /* invalid argument (null pointer, bad size, nfields > max) */
+    ST_ERR_OOM = 2,         /* device allocation failed */
+    ST_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    ST_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    ST_ERR_UNSUPPORTED = 5, /* valid request this build or device cannot serve */
+    ST_ERR_BUSY = 6         /* resource already in use */
+} st_status;
+
+typedef enum { ST_GRID_REGULAR = 0, ST_GRID_OCTAHEDRAL = 1 } st_grid_kind;
+
+typedef enum {
+    ST_FP64 = 0,      /* FP64 everywhere (SIMT Legendre GEMM, FP64 FFT) */
+    ST_FP32_TC = 1,   /* Legendre on tensor cores as 3 x TF32 (hi/lo split), FP32 accumulate */
+    ST_BF16X3 = 2,    /* Legendre on tensor cores as 3 x BF16 (hi/lo split), FP32 accumulate */
+    ST_FP32_SIMT = 3  /* FP32 SIMT Legendre GEMM, FP32 FFT */
+} st_precision;
+
+typedef struct {
+    int kind;  /* st_grid_kind */
+    int nlat;  /* number of Gaussian latitudes (even, >= 2) */
+    int nlon;  /* points per row for ST_GRID_REGULAR; ignored for octahedral grids,
+                  whose row i from either pole (i = 1 .. nlat/2) has 20 + 4 i points */
+} st_grid_desc;
+
+typedef struct {
+    int T, nlat, kind, precision, max_fields;
+    int max_m;                /* largest m kept by any row (min(T, max_j M_j)) */
+    size_t spec_elems;        /* complex coefficients per field: (T+1)(T+2)/2 */
+    size_t grid_points;       /* grid points per field: sum_j N_j */
+    size_t element_bytes;     /* 8 for ST_FP64, else 4 */
+    size_t device_bytes;      /* device memory held by the plan */
+    size_t table_bytes;       /* of which Legendre tables */
+    size_t workspace_bytes;   /* of which workspace */
+} st_plan_info;
+
+/*
+ * Create a plan for truncation T on `grid` (section 4.4.1 statement of the
+ * transform; grid geometry per st_grid_desc).  Builds, on the device and in
+ * FP64, the Gaussian nodes and weights (Newton iteration on P_nlat) and the
+ * normalised associated Legendre tables (three-term recurrence), then
+ * converts them to the layout and precision `prec` needs.  Allocates the
+ * workspace for up to `max_fields` fields per call.  Work runs on `stream`;
+ * the call returns once the plan is ready (it synchronises the stream).
+ * Errors: ST_ERR_ARG for T < 1, odd or too small nlat, nlon < 1 on a regular
+ * grid, unknown kind or precision, max_fields < 1; ST_ERR_OOM; ST_ERR_CUDA;
+ * ST_ERR_UNSUPPORTED if the device is not sm_103 for a tensor-core precision.
+ * On error *out is set to NULL.
+ */
+st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int prec,
+                         int max_fields, void *stream);
+
+/* Release everything the plan holds.  NULL is accepted.  The caller must make
+ * sure no work on the plan is still in flight. */
+st_status st_plan_destroy(st_plan_t plan);
+
+/* Plan facts (sizes, precision, memory). */
+st_status st_plan_query(st_plan_t plan, st_plan_info *info);
+
+/* Copy the row lengths N_j (nlat ints, north to south) to host memory. */
+st_status st_plan_row_lengths(st_plan_t plan, int *rows_host);
+
+/* Copy the device-computed Gaussian nodes mu_j and weights w_j (FP64,
+ * north to south, nlat each) to host memory (synchronous). */
+st_status st_plan_nodes(st_plan_t plan, double *mu_host, double *w_host);
+
+/*
+ * Inverse transform, spectral -> grid (the synthesis equation of section
+ * 4.4.1): spec_dev holds nfields spectral arrays, grid_dev receives nfields
+ * grid arrays (layouts above).  1 <= nfields <= max_fields, else ST_ERR_ARG.
+ * Stages: per-m Legendre GEMMs (section 4.2.4) producing the symmetric and
+ * antisymmetric Fourier coefficients, then per-row inverse real FFTs
+ * (section 4.2.5).  Asynchronous on `stream`.
+ */
+st_status st_inv_trans(st_plan_t plan, const void *spec_dev, void *grid_dev, int nfields,
+                       void *stream);
+
+/*
+ * Direct transform, grid -> spectral (each coefficient the quadrature of the
+ * field against one basis function, section 4.4.2): per-row real FFTs scaled
+ * by 1/N_j, then per-m Legendre GEMMs against w_j Pbar_n^m(mu_j).
+ * Asynchronous on `stream`.  Same argument rules as st_inv_trans.
+ */
+st_status st_dir_trans(st_plan_t plan, const void *grid_dev, void *spec_dev, int nfields,
+                       void *stream);
+
+/* Wait for the plan's work on `stream` and report any device-side error
+ * recorded since the last call (then clear it). */
+st_status st_plan_sync(st_plan_t plan, void *stream);
+
+/* Text for a status code (static storage). */
+const char *st_status_string(st_status s);
+
+/* Last CUDA error text seen by the library on this thread ("" if none). */
+const char *st_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_H */

@@ -1,0 +1,472 @@
+// Plan construction and the C ABI entry points (include/st.h, st_stages.h).
+//
+// A plan holds, on the device and for its whole life, everything that does
+// not change between time steps: Gaussian nodes, Legendre tables in the
+// layout of the chosen precision, per-row FFT data and the workspace.  This is
+// the "reusable arrays" restructuring of ESCAPE D3.3 section 4.2.3 (all
+// allocation and set-up hoisted out of the time-step loop) and the flat,
+// read-only plan metadata of section 4.2.6.4.
+#include "st_internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+namespace st {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &s) { g_last_error = s; }
+
+st_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA;
+}
+
+size_t tc_smem_bytes(int prec, int max_nt, int *stages_out);
+
+static int row_trunc(int T, int n) { return std::min(T, (n - 1) / 2); }
+
+// Factor N into Stockham radices: 4s, then 2, 3, 5, then any other primes.
+static int factorize(int N, int *rad)
+{
+    int n = 0;
+    while (N % 4 == 0 && n < MAX_RADICES) { rad[n++] = 4; N /= 4; }
+    while (N % 2 == 0 && n < MAX_RADICES) { rad[n++] = 2; N /= 2; }
+    while (N % 3 == 0 && n < MAX_RADICES) { rad[n++] = 3; N /= 3; }
+    while (N % 5 == 0 && n < MAX_RADICES) { rad[n++] = 5; N /= 5; }
+    for (int p = 7; (long long)p * p <= N && n < MAX_RADICES; p += 2)
+        while (N % p == 0 && n < MAX_RADICES) { rad[n++] = p; N /= p; }
+    if (N > 1 && n < MAX_RADICES) rad[n++] = N;
+    return n;
+}
+
+template <typename T>
+static st_status dmalloc(st_plan *p, T **ptr, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    p->device_bytes += bytes;
+    return ST_OK;
+}
+
+static void plan_free(st_plan *p)
+{
+    if (!p) return;
+    void *ptrs[] = {p->mu, p->w, p->rowpairs, p->tw, p->tab[0], p->tab[1], p->groups[0], p->groups[1],
+                    p->tiles[0], p->tiles[1], p->fb, p->sbuf, p->err};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+// Group layout for one direction and precision (see LegGroup).
+static void build_groups(st_plan *p, int dir)
+{
+    const int T = p->T, J = p->J;
+    const bool tc = prec_is_tc(p->prec);
+    const int kc = tc ? tc_kc(p->prec) : 1;
+    const int es = p->prec == P_BF16X3 ? 2 : 4;  // tensor-core element bytes
+    (void)es;
+    // inverse column tile: the table columns are the J northern rows
+    int nct_inv = (J + 255) / 256;
+    int nt_inv = ((J + nct_inv - 1) / nct_inv + 15) / 16 * 16;
+
+    std::vector<LegGroup> &G = p->groups_h[dir];
+    G.assign(2 * (T + 1), LegGroup{});
+    long long off = 0;
+    for (int m = 0; m <= T; ++m) {
+        const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
+        const int Ke = (T - m) / 2 + 1, Ko = (T - m + 1) / 2;
+        for (int par = 0; par < 2; ++par) {
+            LegGroup g{};
+            g.m = m;
+            g.p = par;
+            const int Km = par ? Ko : Ke;
+            const long long srow = q0 + (par ? Ke : 0);
+            const long long frow = (long long)(par * (T + 1) + m) * J;
+            const bool live = Km > 0 && m <= p->max_m;
+            if (dir == 0) {
+                g.ncol = J;
+                g.K = Km;
+                g.r0 = 0;
+                g.data_row0 = srow;
+                g.out_row0 = frow;
+            } else {
+                g.ncol = Km;
+                g.K = J;
+                g.r0 = live ? p->j0[m] : 0;
+                g.data_row0 = frow;
+                g.out_row0 = srow;
+            }
+            if (!live) {
+                g.ncol = 0;
+                g.K = 0;
+            }
+            if (tc) {
+                if (dir == 0) {
+                    g.nt = nt_inv;
+                    g.nct = nct_inv;
+                } else {
+                    int n = std::max(g.ncol, 1);
+                    g.nct = (n + 255) / 256;
+                    g.nt = ((n + g.nct - 1) / g.nct + 15) / 16 * 16;
+                }
+                g.nkc = (std::max(g.K, 1) + kc - 1) / kc;
+                g.tab_off = off;
+                if (live) off += (long long)g.nct * g.nkc * 2 * g.nt * 128;
+            } else {
+                g.nt = SIMT_TILE;
+                g.nct = (std::max(g.ncol, 1) + SIMT_TILE - 1) / SIMT_TILE;
+                g.nkc = 0;
+                g.tab_off = off;
+                if (live) off += (long long)g.ncol * g.K;
+            }
+            G[2 * m + par] = g;
+        }
+    }
+    const size_t el = tc ? 1 : (p->prec == P_FP64 ? 8 : 4);
+    p->tab_bytes[dir] = (size_t)off * el;
+}
+
+// Work list (group, column tile), heaviest first.
+static std::vector<LegTile> build_tiles(const st_plan *p, int dir)
+{
+    const bool tc = prec_is_tc(p->prec);
+    const int kc = tc ? tc_kc(p->prec) : 16;
+    std::vector<std::pair<long long, LegTile>> v;
+    const auto &G = p->groups_h[dir];
+    for (int gi = 0; gi < (int)G.size(); ++gi) {
+        const LegGroup &g = G[gi];
+        if (g.ncol <= 0 || g.K <= 0) continue;
+        int ct0 = 0;
+        if (dir == 0) ct0 = p->j0[g.m] / g.nt;  // rows nearer the pole than j0(m) do not keep m
+        const long long chunks = (g.K + kc - 1) / kc - g.r0 / kc;
+        for (int ct = ct0; ct < g.nct; ++ct) v.push_back({chunks * g.nt, LegTile{gi, ct}});
+    }
+    std::stable_sort(v.begin(), v.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<LegTile> out;
+    out.reserve(v.size());
+    for (auto &e : v) out.push_back(e.second);
+    return out;
+}
+
+static st_status plan_build(st_plan *p, cudaStream_t s)
+{
+    const int T = p->T, nlat = p->nlat, J = nlat / 2;
+    p->J = J;
+    p->rows.resize(nlat);
+    for (int j = 0; j < nlat; ++j) {
+        if (p->kind == ST_GRID_REGULAR) p->rows[j] = p->nlon;
+        else p->rows[j] = 20 + 4 * (std::min(j, nlat - 1 - j) + 1);
+    }
+    p->npts = 0;
+    for (int n : p->rows) p->npts += n;
+    p->nspec = (long long)(T + 1) * (T + 2) / 2;
+    p->Mrow.resize(J);
+    p->max_m = -1;
+    for (int j = 0; j < J; ++j) {
+        p->Mrow[j] = row_trunc(T, p->rows[j]);
+        p->max_m = std::max(p->max_m, p->Mrow[j]);
+    }
+    if (p->max_m < 0) return ST_ERR_ARG;
+    p->j0.assign(T + 1, J);
+    for (int m = 0; m <= T; ++m)
+        for (int j = 0; j < J; ++j)
+            if (p->Mrow[j] >= m) { p->j0[m] = j; break; }
+
+    st_status r;
+    if ((r = dmalloc(p, &p->err, sizeof(int)))) return r;
+    ST_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+
+    // nodes and weights
+    if ((r = dmalloc(p, &p->mu, sizeof(double) * nlat))) return r;
+    if ((r = dmalloc(p, &p->w, sizeof(double) * nlat))) return r;
+    if ((r = launch_gauss(nlat, p->mu, p->w, s))) return r;
+
+    // FFT rows
+    p->rowpairs_h.resize(J);
+    long long off = 0, tw = 0;
+    std::vector<long long> roff(nlat);
+    for (int j = 0; j < nlat; ++j) { roff[j] = off; off += p->rows[j]; }
+    p->max_row = 0;
+    for (int j = 0; j < J; ++j) {
+        RowPair &rp = p->rowpairs_h[j];
+        memset(&rp, 0, sizeof(rp));
+        rp.N = p->rows[j];
+        rp.M = p->Mrow[j];
+        rp.nrad = factorize(rp.N, rp.rad);
+        rp.tw_off = tw;
+        rp.off_n = roff[j];
+        rp.off_s = roff[nlat - 1 - j];
+        tw += rp.N;
+        p->max_row = std::max(p->max_row, rp.N);
+        int prod = 1;
+        for (int q = 0; q < rp.nrad; ++q) prod *= rp.rad[q];
+        if (prod != rp.N) return ST_ERR_UNSUPPORTED;
+    }
+    p->ntw = tw;
+    if ((r = dmalloc(p, &p->rowpairs, sizeof(RowPair) * J))) return r;
+    ST_CUDA(cudaMemcpyAsync(p->rowpairs, p->rowpairs_h.data(), sizeof(RowPair) * J, cudaMemcpyHostToDevice, s));
+    if ((r = dmalloc(p, &p->tw, (p->prec == P_FP64 ? 16 : 8) * (size_t)tw))) return r;
+    if ((r = launch_twiddles(p, s))) return r;
+
+    // Legendre groups, tiles, tables
+    for (int dir = 0; dir < 2; ++dir) {
+        build_groups(p, dir);
+        std::vector<LegTile> tl = build_tiles(p, dir);
+        p->ntiles[dir] = (int)tl.size();
+        if ((r = dmalloc(p, &p->groups[dir], sizeof(LegGroup) * p->groups_h[dir].size()))) return r;
+        ST_CUDA(cudaMemcpyAsync(p->groups[dir], p->groups_h[dir].data(), sizeof(LegGroup) * p->groups_h[dir].size(),
+                                cudaMemcpyHostToDevice, s));
+        if ((r = dmalloc(p, &p->tiles[dir], sizeof(LegTile) * std::max<size_t>(tl.size(), 1)))) return r;
+        if (!tl.empty())
+            ST_CUDA(cudaMemcpyAsync(p->tiles[dir], tl.data(), sizeof(LegTile) * tl.size(), cudaMemcpyHostToDevice, s));
+        // the host copy of the tile list must outlive the async copy
+        ST_CUDA(cudaStreamSynchronize(s));
+        if ((r = dmalloc(p, &p->tab[dir], p->tab_bytes[dir]))) return r;
+        ST_CUDA(cudaMemsetAsync(p->tab[dir], 0, std::max<size_t>(p->tab_bytes[dir], 16), s));
+        p->table_bytes += p->tab_bytes[dir];
+    }
+    if ((r = launch_tables(p, s))) return r;
+
+    // workspace
+    const int Cp = cols_padded(p->max_fields);
+    const int sb = store_bytes(store_of(p->prec)) * store_planes(store_of(p->prec));
+    const int ob = p->prec == P_FP64 ? 8 : 4;
+    const size_t per = (size_t)std::max(sb, ob);
+    p->fb_bytes = (size_t)fb_rows(p) * Cp * per;
+    p->sbuf_bytes = (size_t)p->nspec * Cp * per;
+    if ((r = dmalloc(p, &p->fb, p->fb_bytes))) return r;
+    if ((r = dmalloc(p, &p->sbuf, p->sbuf_bytes))) return r;
+    ST_CUDA(cudaMemsetAsync(p->fb, 0, p->fb_bytes, s));
+    ST_CUDA(cudaMemsetAsync(p->sbuf, 0, p->sbuf_bytes, s));
+    p->workspace_bytes = p->fb_bytes + p->sbuf_bytes;
+
+    if (prec_is_tc(p->prec)) {
+        for (int dir = 0; dir < 2; ++dir) {
+            int mx = 16;
+            for (const auto &g : p->groups_h[dir]) mx = std::max(mx, g.nt);
+            int S = 0;
+            tc_smem_bytes(p->prec, mx, &S);
+            if (S < 2) return ST_ERR_UNSUPPORTED;
+        }
+    }
+    ST_CUDA(cudaStreamSynchronize(s));
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+static st_status check_fields(st_plan_t p, int nfields)
+{
+    if (!p) return ST_ERR_ARG;
+    if (nfields < 1 || nfields > p->max_fields) {
+        set_last_error("nfields out of range");
+        return ST_ERR_ARG;
+    }
+    return ST_OK;
+}
+
+static st_status leg(st_plan *p, int dir, int nfields, cudaStream_t s)
+{
+    return prec_is_tc(p->prec) ? launch_leg_tc(p, dir, nfields, s) : launch_leg_simt(p, dir, nfields, s);
+}
+
+}  // namespace st
+
+using namespace st;
+
+extern "C" {
+
+const char *st_status_string(st_status s)
+{
+    switch (s) {
+    case ST_OK: return "ok";
+    case ST_ERR_ARG: return "invalid argument";
+    case ST_ERR_OOM: return "out of device memory";
+    case ST_ERR_CUDA: return "CUDA error";
+    case ST_ERR_TIMEOUT: return "device-side wait timed out";
+    case ST_ERR_UNSUPPORTED: return "unsupported";
+    case ST_ERR_BUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+const char *st_last_error(void) { return g_last_error.c_str(); }
+
+st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int prec, int max_fields, void *stream)
+{
+    if (!out) return ST_ERR_ARG;
+    *out = nullptr;
+    if (!grid || T < 1 || grid->nlat < 2 || (grid->nlat & 1) || max_fields < 1 || prec < 0 || prec > 3 ||
+        (grid->kind != ST_GRID_REGULAR && grid->kind != ST_GRID_OCTAHEDRAL) ||
+        (grid->kind == ST_GRID_REGULAR && grid->nlon < 1) || T > 4095 || grid->nlat > 8192 ||
+        (grid->kind == ST_GRID_REGULAR && grid->nlon > 65536)) {
+        set_last_error("invalid plan arguments");
+        return ST_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    st_plan *p = new st_plan();
+    p->T = T;
+    p->nlat = grid->nlat;
+    p->kind = grid->kind;
+    p->nlon = grid->kind == ST_GRID_REGULAR ? grid->nlon : 0;
+    p->prec = prec;
+    p->max_fields = max_fields;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaGetDevice"); }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, p->device);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaGetDeviceProperties"); }
+    p->sm_count = prop.multiProcessorCount;
+    if (prec_is_tc(prec) && !(prop.major == 10 && prop.minor == 3)) {
+        set_last_error("tensor-core precisions need an sm_103 device");
+        plan_free(p);
+        return ST_ERR_UNSUPPORTED;
+    }
+    st_status r = plan_build(p, s);
+    if (r != ST_OK) {
+        cudaStreamSynchronize(s);
+        plan_free(p);
+        return r;
+    }
+    *out = p;
+    return ST_OK;
+}
+
+st_status st_plan_destroy(st_plan_t p)
+{
+    plan_free(p);
+    return ST_OK;
+}
+
+st_status st_plan_query(st_plan_t p, st_plan_info *info)
+{
+    if (!p || !info) return ST_ERR_ARG;
+    info->T = p->T;
+    info->nlat = p->nlat;
+    info->kind = p->kind;
+    info->precision = p->prec;
+    info->max_fields = p->max_fields;
+    info->max_m = p->max_m;
+    info->spec_elems = (size_t)p->nspec;
+    info->grid_points = (size_t)p->npts;
+    info->element_bytes = p->prec == P_FP64 ? 8 : 4;
+    info->device_bytes = p->device_bytes;
+    info->table_bytes = p->table_bytes;
+    info->workspace_bytes = p->workspace_bytes;
+    return ST_OK;
+}
+
+st_status st_plan_row_lengths(st_plan_t p, int *rows_host)
+{
+    if (!p || !rows_host) return ST_ERR_ARG;
+    memcpy(rows_host, p->rows.data(), sizeof(int) * p->nlat);
+    return ST_OK;
+}
+
+st_status st_plan_nodes(st_plan_t p, double *mu_host, double *w_host)
+{
+    if (!p || !mu_host || !w_host) return ST_ERR_ARG;
+    ST_CUDA(cudaMemcpy(mu_host, p->mu, sizeof(double) * p->nlat, cudaMemcpyDeviceToHost));
+    ST_CUDA(cudaMemcpy(w_host, p->w, sizeof(double) * p->nlat, cudaMemcpyDeviceToHost));
+    return ST_OK;
+}
+
+st_status st_inv_trans(st_plan_t p, const void *spec_dev, void *grid_dev, int nfields, void *stream)
+{
+    st_status r = check_fields(p, nfields);
+    if (r) return r;
+    if (!spec_dev || !grid_dev) return ST_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = launch_pack(p, spec_dev, nfields, s))) return r;
+    if ((r = leg(p, 0, nfields, s))) return r;
+    return launch_fft_inv(p, grid_dev, nfields, s);
+}
+
+st_status st_dir_trans(st_plan_t p, const void *grid_dev, void *spec_dev, int nfields, void *stream)
+{
+    st_status r = check_fields(p, nfields);
+    if (r) return r;
+    if (!spec_dev || !grid_dev) return ST_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = launch_fft_dir(p, grid_dev, nfields, s))) return r;
+    if ((r = leg(p, 1, nfields, s))) return r;
+    return launch_unpack(p, spec_dev, nfields, s);
+}
+
+st_status st_plan_sync(st_plan_t p, void *stream)
+{
+    if (!p) return ST_ERR_ARG;
+    ST_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int e = 0;
+    ST_CUDA(cudaMemcpy(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        ST_CUDA(cudaMemset(p->err, 0, sizeof(int)));
+        set_last_error("device-side wait timed out (flags " + std::to_string(e) + ")");
+        return ST_ERR_TIMEOUT;
+    }
+    return ST_OK;
+}
+
+// ---- stages
+
+st_status st_gauss_nodes(int nlat, double *mu_dev, double *w_dev, void *stream)
+{
+    if (nlat < 2 || !mu_dev || !w_dev) return ST_ERR_ARG;
+    return launch_gauss(nlat, mu_dev, w_dev, (cudaStream_t)stream);
+}
+
+st_status st_legendre_values(int T, const double *mu_dev, int nmu, double *out_dev, void *stream)
+{
+    if (T < 0 || nmu < 1 || !mu_dev || !out_dev) return ST_ERR_ARG;
+    return launch_legendre_values(T, mu_dev, nmu, out_dev, (cudaStream_t)stream);
+}
+
+st_status st_inv_legendre(st_plan_t p, const void *spec_dev, int nfields, void *stream)
+{
+    st_status r = check_fields(p, nfields);
+    if (r) return r;
+    if (!spec_dev) return ST_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = launch_pack(p, spec_dev, nfields, s))) return r;
+    return leg(p, 0, nfields, s);
+}
+
+st_status st_inv_fft(st_plan_t p, void *grid_dev, int nfields, void *stream)
+{
+    st_status r = check_fields(p, nfields);
+    if (r) return r;
+    if (!grid_dev) return ST_ERR_ARG;
+    return launch_fft_inv(p, grid_dev, nfields, (cudaStream_t)stream);
+}
+
+st_status st_dir_fft(st_plan_t p, const void *grid_dev, int nfields, void *stream)
+{
+    st_status r = check_fields(p, nfields);
+    if (r) return r;
+    if (!grid_dev) return ST_ERR_ARG;
+    return launch_fft_dir(p, grid_dev, nfields, (cudaStream_t)stream);
+}
+
+st_status st_dir_legendre(st_plan_t p, void *spec_dev, int nfields, void *stream)
+{
+    st_status r = check_fields(p, nfields);
+    if (r) return r;
+    if (!spec_dev) return ST_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((r = leg(p, 1, nfields, s))) return r;
+    return launch_unpack(p, spec_dev, nfields, s);
+}
+
+st_status st_fourier_export(st_plan_t p, int direction, int nfields, double *out_dev, void *stream)
+{
+    st_status r = check_fields(p, nfields);
+    if (r) return r;
+    if (!out_dev || direction < 0 || direction > 1) return ST_ERR_ARG;
+    return launch_fourier_export(p, direction, nfields, out_dev, (cudaStream_t)stream);
+}
+
+}  // extern "C"

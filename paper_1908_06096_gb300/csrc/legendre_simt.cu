@@ -1,0 +1,289 @@
+// Legendre stage on the SIMT cores (the plain FP64 form and the FP32 SIMT
+// form), the spectral pack/unpack that lay the coefficients out as GEMM
+// operands, and the Fourier-buffer export used by the parity tests.
+//
+// The Legendre transform of ESCAPE D3.3 section 4.2.4 is one matrix product
+// per zonal wavenumber m.  Splitting n - m into even and odd halves (using
+// Pbar_n^m(-mu) = (-1)^(n-m) Pbar_n^m(mu)) gives two products per m over the
+// northern rows only, which halves the work; all (m, parity) products run in
+// one launch, each tile looking up its group (the grouped form of section
+// 4.2.4's batched GEMM, without zero padding to a common size).
+#include "st_internal.cuh"
+
+namespace st {
+
+// ---------------------------------------------------------------- SIMT GEMM
+
+// out[col][c] = sum_r tab[col][r] * data[r][c] for one (group, column tile,
+// data tile) per CTA; 64 x 64 outputs, 256 threads with 4 x 4 each.
+template <typename Rr>
+__global__ void __launch_bounds__(256) k_leg_simt(const LegGroup *__restrict__ groups, const LegTile *__restrict__ tiles,
+                                                  int ncm, const Rr *__restrict__ tab, const Rr *__restrict__ data,
+                                                  Rr *__restrict__ out, int C, int Cp)
+{
+    constexpr int TB = SIMT_TILE, KB = 16;
+    __shared__ Rr As[KB][TB + 1];
+    __shared__ Rr Bs[KB][TB];
+    const int tile = blockIdx.x;
+    const LegTile lt = tiles[tile / ncm];
+    const int cm = tile % ncm;
+    const LegGroup g = groups[lt.g];
+    const int col0 = lt.ct * TB, c0 = cm * TB;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    Rr acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+
+    const Rr *tg = tab + g.tab_off;
+    for (int r = g.r0; r < g.K; r += KB) {
+        for (int e = threadIdx.x; e < TB * KB; e += 256) {
+            int cc = e / KB, kk = e % KB;
+            int col = col0 + cc, rr = r + kk;
+            As[kk][cc] = (col < g.ncol && rr < g.K) ? tg[(long long)col * g.K + rr] : (Rr)0;
+        }
+        for (int e = threadIdx.x; e < TB * KB; e += 256) {
+            int kk = e / TB, c = e % TB;
+            int rr = r + kk, cg = c0 + c;
+            Bs[kk][c] = (rr < g.K && cg < C) ? data[(g.data_row0 + rr) * (long long)Cp + cg] : (Rr)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KB; ++kk) {
+            Rr a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] = As[kk][ty * 4 + q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = Bs[kk][tx * 4 + q];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int col = col0 + ty * 4 + u;
+        if (col >= g.ncol) continue;
+        Rr *o = out + (g.out_row0 + col) * (long long)Cp;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int c = c0 + tx * 4 + v;
+            if (c < C) o[c] = acc[u][v];
+        }
+    }
+}
+
+st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s)
+{
+    int C = 2 * nfields, Cp = cols_padded(nfields);
+    int ncm = (C + SIMT_TILE - 1) / SIMT_TILE;
+    long long nt = (long long)p->ntiles[dir] * ncm;
+    if (nt == 0) return ST_OK;
+    if (nt > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
+    // inverse: data = packed spectra, out = Fourier buffer; direct: the reverse
+    void *data = dir == 0 ? p->sbuf : p->fb;
+    void *out = dir == 0 ? p->fb : p->sbuf;
+    if (p->prec == P_FP64)
+        k_leg_simt<double><<<(unsigned)nt, 256, 0, s>>>(p->groups[dir], p->tiles[dir], ncm, (const double *)p->tab[dir],
+                                                        (const double *)data, (double *)out, C, Cp);
+    else
+        k_leg_simt<float><<<(unsigned)nt, 256, 0, s>>>(p->groups[dir], p->tiles[dir], ncm, (const float *)p->tab[dir],
+                                                       (const float *)data, (float *)out, C, Cp);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- pack / unpack
+
+__device__ inline float round_tf32_p(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int S, typename Rr>
+__device__ inline void put_op(void *base, long long idx, long long ps, Rr v)
+{
+    if (S == S_F64) {
+        ((double *)base)[idx] = (double)v;
+    } else if (S == S_F32) {
+        ((float *)base)[idx] = (float)v;
+    } else if (S == S_TF32_SPLIT) {
+        float f = (float)v, hi = round_tf32_p(f), lo = round_tf32_p(f - hi);
+        ((float *)base)[idx] = hi;
+        ((float *)base)[idx + ps] = lo;
+    } else {
+        float f = (float)v;
+        __nv_bfloat16 hi = __float2bfloat16_rn(f);
+        __nv_bfloat16 lo = __float2bfloat16_rn(f - __bfloat162float(hi));
+        ((__nv_bfloat16 *)base)[idx] = hi;
+        ((__nv_bfloat16 *)base)[idx + ps] = lo;
+    }
+}
+
+// Spectra [field][(m,n)][re,im] -> operand rows: row of (m, n) is
+// q(m,m) + k for n - m = 2k (even half), q(m,m) + K_m^e + k for n - m = 2k+1;
+// column 2 f + (re, im).  One CTA per (m, 32-field tile); smem transpose.
+template <typename Rr, int S>
+__global__ void __launch_bounds__(256) k_pack(int T, const Rr *__restrict__ spec, int nfields, long long nspec,
+                                              void *out, int Cp, long long ps)
+{
+    __shared__ Rr tile[32][65];
+    const int m = blockIdx.y;
+    const int f0 = blockIdx.x * 32;
+    const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
+    const int len = T - m + 1;
+    const int Ke = (T - m) / 2 + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d0 = 0; d0 < len; d0 += 32) {
+        // load: warp w reads fields w, w+8, ...; lane = d
+        for (int ff = warp; ff < 32; ff += 8) {
+            int fld = f0 + ff, d = d0 + lane;
+            Rr re = 0, im = 0;
+            if (fld < nfields && d < len) {
+                const Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
+                re = a[0];
+                im = m == 0 ? (Rr)0 : a[1];
+            }
+            tile[lane][2 * ff] = re;
+            tile[lane][2 * ff + 1] = im;
+        }
+        __syncthreads();
+        // store: warp w writes rows d = w, w+8, ...; lanes cover 64 columns
+        for (int dd = warp; dd < 32; dd += 8) {
+            int d = d0 + dd;
+            if (d >= len) continue;
+            long long row = q0 + ((d & 1) ? Ke + (d >> 1) : (d >> 1));
+            for (int cc = lane; cc < 64; cc += 32) {
+                int c = 2 * f0 + cc;
+                if (c < 2 * nfields) put_op<S, Rr>(out, row * Cp + c, ps, tile[dd][cc]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Operand rows (direct GEMM output, FP32/FP64) -> spectra.  Wavenumbers kept
+// by no row (m > max_m) are written as zero; Im a_n^0 is written as zero.
+template <typename Rr>
+__global__ void __launch_bounds__(256) k_unpack(int T, int max_m, const Rr *__restrict__ in, int Cp, int nfields,
+                                                long long nspec, Rr *__restrict__ spec)
+{
+    __shared__ Rr tile[32][65];
+    const int m = blockIdx.y;
+    const int f0 = blockIdx.x * 32;
+    const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
+    const int len = T - m + 1;
+    const int Ke = (T - m) / 2 + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool zero = m > max_m;
+    for (int d0 = 0; d0 < len; d0 += 32) {
+        for (int dd = warp; dd < 32; dd += 8) {
+            int d = d0 + dd;
+            long long row = q0 + ((d & 1) ? Ke + (d >> 1) : (d >> 1));
+            for (int cc = lane; cc < 64; cc += 32) {
+                int c = 2 * f0 + cc;
+                Rr v = 0;
+                if (!zero && d < len && c < 2 * nfields) v = in[row * Cp + c];
+                tile[dd][cc] = v;
+            }
+        }
+        __syncthreads();
+        for (int ff = warp; ff < 32; ff += 8) {
+            int fld = f0 + ff, d = d0 + lane;
+            if (fld < nfields && d < len) {
+                Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
+                a[0] = tile[lane][2 * ff];
+                a[1] = m == 0 ? (Rr)0 : tile[lane][2 * ff + 1];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s)
+{
+    int Cp = cols_padded(nfields);
+    long long ps = p->nspec * Cp;
+    dim3 g((nfields + 31) / 32, p->max_m + 1);
+    switch (p->prec) {
+    case P_FP64:
+        k_pack<double, S_F64><<<g, 256, 0, s>>>(p->T, (const double *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        break;
+    case P_FP32:
+        k_pack<float, S_F32><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        break;
+    case P_TF32X3:
+        k_pack<float, S_TF32_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        break;
+    default:
+        k_pack<float, S_BF16_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        break;
+    }
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+st_status launch_unpack(st_plan *p, void *spec, int nfields, cudaStream_t s)
+{
+    int Cp = cols_padded(nfields);
+    dim3 g((nfields + 31) / 32, p->T + 1);
+    if (p->prec == P_FP64)
+        k_unpack<double><<<g, 256, 0, s>>>(p->T, p->max_m, (const double *)p->sbuf, Cp, nfields, p->nspec,
+                                           (double *)spec);
+    else
+        k_unpack<float><<<g, 256, 0, s>>>(p->T, p->max_m, (const float *)p->sbuf, Cp, nfields, p->nspec,
+                                          (float *)spec);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- export (tests)
+
+__global__ void k_fourier_export(int T, int J, const int *Mrow, int store, const void *fb, int Cp, long long ps,
+                                 int nfields, double *out)
+{
+    long long total = 2LL * (T + 1) * J * nfields;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        int f = (int)(i % nfields);
+        long long r = i / nfields;  // (p, m, j) row
+        int j = (int)(r % J);
+        int m = (int)((r / J) % (T + 1));
+        double v[2] = {0.0, 0.0};
+        if (m <= Mrow[j]) {
+            for (int q = 0; q < 2; ++q) {
+                long long idx = r * Cp + 2 * f + q;
+                if (store == S_F64) v[q] = ((const double *)fb)[idx];
+                else if (store == S_F32) v[q] = ((const float *)fb)[idx];
+                else if (store == S_TF32_SPLIT)
+                    v[q] = (double)((const float *)fb)[idx] + (double)((const float *)fb)[idx + ps];
+                else
+                    v[q] = (double)__bfloat162float(((const __nv_bfloat16 *)fb)[idx]) +
+                           (double)__bfloat162float(((const __nv_bfloat16 *)fb)[idx + ps]);
+            }
+        }
+        out[2 * i] = v[0];
+        out[2 * i + 1] = v[1];
+    }
+}
+
+st_status launch_fourier_export(st_plan *p, int dir, int nfields, double *out, cudaStream_t s)
+{
+    int *Mrow_d = nullptr;
+    ST_CUDA(cudaMallocAsync(&Mrow_d, sizeof(int) * p->J, s));
+    ST_CUDA(cudaMemcpyAsync(Mrow_d, p->Mrow.data(), sizeof(int) * p->J, cudaMemcpyHostToDevice, s));
+    int Cp = cols_padded(nfields);
+    int store = dir == 0 ? (p->prec == P_FP64 ? S_F64 : S_F32) : store_of(p->prec);
+    long long ps = fb_rows(p) * Cp;
+    k_fourier_export<<<1024, 256, 0, s>>>(p->T, p->J, Mrow_d, store, p->fb, Cp, ps, nfields, out);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(Mrow_d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_fourier_export");
+    return ST_OK;
+}
+
+}  // namespace st

@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of the
+// spherical-harmonic transform library.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "st.h"
+#include "st_stages.h"
+
+namespace st {
+
+enum Prec { P_FP64 = 0, P_TF32X3 = 1, P_BF16X3 = 2, P_FP32 = 3 };
+
+// Storage modes of a data operand written for the Legendre stage.
+enum Store { S_F64 = 0, S_F32 = 1, S_TF32_SPLIT = 2, S_BF16_SPLIT = 3 };
+
+inline int store_of(int prec)
+{
+    switch (prec) {
+    case P_FP64: return S_F64;
+    case P_TF32X3: return S_TF32_SPLIT;
+    case P_BF16X3: return S_BF16_SPLIT;
+    default: return S_F32;
+    }
+}
+inline int store_bytes(int s) { return s == S_F64 ? 8 : (s == S_BF16_SPLIT ? 2 : 4); }
+inline int store_planes(int s) { return (s == S_TF32_SPLIT || s == S_BF16_SPLIT) ? 2 : 1; }
+inline bool prec_is_tc(int prec) { return prec == P_TF32X3 || prec == P_BF16X3; }
+
+constexpr int MAX_RADICES = 24;
+
+// One northern Gaussian row j (0 = nearest the pole) and its mirror row
+// nlat-1-j; both have N points.
+struct RowPair {
+    int N;                    // points per row
+    int M;                    // wavenumbers kept: 0..M
+    int nrad;                 // number of Stockham passes
+    int rad[MAX_RADICES];     // radix of each pass
+    long long tw_off;         // first of the row's N roots of unity e^{-2 pi i t / N}
+    long long off_n;          // offset of the northern row inside one field's grid
+    long long off_s;          // offset of the southern row
+};
+
+// One Legendre GEMM: zonal wavenumber m, parity p (n - m even: 0, odd: 1),
+// in one direction.  out[col][c] = sum_r tab[col][r] * data[r][c].
+//   inverse: col = northern row j (ncol = J), r = k with n = m + p + 2k
+//   direct:  col = k (ncol = K_m^p), r = northern row j (K = J)
+struct LegGroup {
+    int m, p;
+    int ncol;                 // valid columns of the table
+    int K;                    // valid reduction length
+    int r0;                   // first reduction index worth visiting (row trimming)
+    int nt;                   // column-tile width (tensor-core layout)
+    int nct;                  // number of column tiles
+    int nkc;                  // number of reduction chunks in the stored table
+    long long data_row0;      // data-operand row holding reduction index 0
+    long long out_row0;       // output row holding column 0
+    long long tab_off;        // table offset: elements (SIMT) or bytes (tensor-core images)
+};
+
+struct LegTile {
+    int g;                    // group index (2 m + p)
+    int ct;                   // column tile
+};
+
+}  // namespace st
+
+// The plan object behind st_plan_t.
+struct st_plan {
+    int T = 0, nlat = 0, J = 0, kind = 0, nlon = 0, prec = 0, max_fields = 0;
+    int max_m = 0;
+    int device = 0, sm_count = 0;
+    std::vector<int> rows;     // nlat row lengths
+    std::vector<int> Mrow;     // J kept wavenumbers of each northern row
+    std::vector<int> j0;       // T+1: first northern row with M_j >= m (J if none)
+    long long npts = 0;        // grid points per field
+    long long nspec = 0;       // complex coefficients per field
+
+    double *mu = nullptr, *w = nullptr;  // device FP64 nodes and weights (nlat)
+
+    // FFT data
+    st::RowPair *rowpairs = nullptr;     // device, J entries
+    std::vector<st::RowPair> rowpairs_h;
+    void *tw = nullptr;                  // device roots of unity (double2 or float2)
+    long long ntw = 0;
+    int max_row = 0;
+
+    // Legendre data, [0] inverse, [1] direct
+    void *tab[2] = {nullptr, nullptr};
+    size_t tab_bytes[2] = {0, 0};
+    st::LegGroup *groups[2] = {nullptr, nullptr};
+    std::vector<st::LegGroup> groups_h[2];
+    st::LegTile *tiles[2] = {nullptr, nullptr};
+    int ntiles[2] = {0, 0};
+
+    // workspace
+    void *fb = nullptr;       // Fourier buffer: 2 (T+1) J rows x Cp columns (x planes)
+    size_t fb_bytes = 0;
+    void *sbuf = nullptr;     // packed spectra: nspec rows x Cp columns (x planes)
+    size_t sbuf_bytes = 0;
+    int *err = nullptr;       // device error word (bit flags set by bounded waits)
+
+    size_t device_bytes = 0, table_bytes = 0, workspace_bytes = 0;
+};
+
+namespace st {
+
+// ---- error plumbing (host) ----
+void set_last_error(const std::string &s);
+st_status cuda_fail(cudaError_t e, const char *what);
+#define ST_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return st::cuda_fail(e_, #call);    \
+    } while (0)
+
+inline long long fb_rows(const st_plan *p) { return 2LL * (p->T + 1) * p->J; }
+inline int cols_padded(int nfields) { return ((2 * nfields + 7) / 8) * 8; }
+
+// Tensor-core Legendre kernel geometry: 128 data columns per tile; a reduction
+// chunk is 128 bytes of the K-major table row (64 bf16 or 32 tf32 values).
+constexpr int TC_M = 128;
+inline int tc_kc(int prec) { return prec == P_BF16X3 ? 64 : 32; }
+constexpr int SIMT_TILE = 64;
+
+// ---- launchers implemented in the .cu files ----
+st_status launch_tables(st_plan *p, cudaStream_t s);
+st_status launch_twiddles(st_plan *p, cudaStream_t s);
+st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s);
+st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s);
+st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s);
+st_status launch_unpack(st_plan *p, void *spec, int nfields, cudaStream_t s);
+st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s);
+st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s);
+st_status launch_fourier_export(st_plan *p, int dir, int nfields, double *out, cudaStream_t s);
+st_status launch_gauss(int nlat, double *mu, double *w, cudaStream_t s);
+st_status launch_legendre_values(int T, const double *mu, int nmu, double *out, cudaStream_t s);
+
+}  // namespace st

@@ -1,0 +1,246 @@
+// Plan-time kernels, all in FP64: Gaussian nodes and weights, normalised
+// associated Legendre values, the Legendre tables in the layout each
+// precision's GEMM reads, and the FFT roots of unity.
+//
+// Gaussian quadrature and the normalised associated Legendre functions are
+// the ingredients of the transform of ESCAPE D3.3 section 4.4.1 (synthesis
+// equation) and section 4.4.2 (coefficients as inner products); the paper
+// does not spell out how they are computed.  Here: Newton iteration on
+// P_nlat for the nodes, and the standard three-term recurrence in n for
+// Pbar_n^m, both in FP64, once per plan.
+#include "st_internal.cuh"
+
+namespace st {
+
+// ---------------------------------------------------------------- nodes
+
+__device__ static void leg_p_and_prev(int n, double x, double &pn, double &pnm1)
+{
+    double p0 = 1.0, p1 = x;
+    if (n == 0) { pn = 1.0; pnm1 = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    pn = p1;
+    pnm1 = p0;
+}
+
+// One thread per northern root; Newton from cos(pi (j - 1/4) / (nlat + 1/2)),
+// until the step is below 1e-15, plus one more step.  w = 2 / ((1 - x^2) P'^2).
+__global__ void k_gauss(int nlat, double *mu, double *w)
+{
+    int half = (nlat + 1) / 2;
+    int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (j > half) return;
+    double x = cospi((j - 0.25) / (nlat + 0.5));
+    double pn, pnm1, dp;
+    bool extra = false;
+    for (int it = 0; it < 100; ++it) {
+        leg_p_and_prev(nlat, x, pn, pnm1);
+        dp = nlat * (x * pn - pnm1) / (x * x - 1.0);
+        double dx = pn / dp;
+        x -= dx;
+        if (extra) break;
+        if (fabs(dx) < 1e-15) extra = true;
+    }
+    leg_p_and_prev(nlat, x, pn, pnm1);
+    dp = nlat * (x * pn - pnm1) / (x * x - 1.0);
+    double wj = 2.0 / ((1.0 - x * x) * dp * dp);
+    if ((nlat & 1) && j == half) x = 0.0;
+    mu[j - 1] = x;
+    w[j - 1] = wj;
+    mu[nlat - j] = -x;
+    w[nlat - j] = wj;
+}
+
+st_status launch_gauss(int nlat, double *mu, double *w, cudaStream_t s)
+{
+    int half = (nlat + 1) / 2;
+    k_gauss<<<(half + 127) / 128, 128, 0, s>>>(nlat, mu, w);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- Pbar recurrence
+
+// Walks n = m .. T for one (m, mu) and hands each Pbar_n^m(mu) to `emit`.
+//   Pbar_0^0 = 1/sqrt(2);  Pbar_m^m = sqrt((2m+1)/(2m)) sin(theta) Pbar_{m-1}^{m-1}
+//   Pbar_{m+1}^m = sqrt(2m+3) mu Pbar_m^m
+//   Pbar_n^m = sqrt((4n^2-1)/(n^2-m^2)) (mu Pbar_{n-1}^m
+//              - sqrt(((n-1)^2-m^2)/(4(n-1)^2-1)) Pbar_{n-2}^m)
+template <class F>
+__device__ inline void pbar_column(int T, int m, double x, F emit)
+{
+    double s = sqrt((1.0 - x) * (1.0 + x));
+    double pmm = 0.70710678118654752440;  // 1/sqrt(2)
+    for (int k = 1; k <= m; ++k) pmm = sqrt((2.0 * k + 1.0) / (2.0 * k)) * s * pmm;
+    emit(m, pmm);
+    if (m + 1 > T) return;
+    double p1 = sqrt(2.0 * m + 3.0) * x * pmm;
+    emit(m + 1, p1);
+    double p0 = pmm;
+    double mm = (double)m * m;
+    for (int n = m + 2; n <= T; ++n) {
+        double dn = n, dn1 = n - 1.0;
+        double a = sqrt((4.0 * dn * dn - 1.0) / (dn * dn - mm));
+        double b = sqrt((dn1 * dn1 - mm) / (4.0 * dn1 * dn1 - 1.0));
+        double p2 = a * (x * p1 - b * p0);
+        emit(n, p2);
+        p0 = p1;
+        p1 = p2;
+    }
+}
+
+__device__ inline long long tri_index(int T, int m, int n)
+{
+    return (long long)m * (T + 1) - (long long)m * (m - 1) / 2 + (n - m);
+}
+
+__global__ void k_legendre_values(int T, const double *mu, int nmu, double *out)
+{
+    int m = blockIdx.y;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nmu || m > T) return;
+    long long ns = (long long)(T + 1) * (T + 2) / 2;
+    double *o = out + (long long)i * ns;
+    pbar_column(T, m, mu[i], [&](int n, double v) { o[tri_index(T, m, n)] = v; });
+}
+
+st_status launch_legendre_values(int T, const double *mu, int nmu, double *out, cudaStream_t s)
+{
+    dim3 grid((nmu + 127) / 128, T + 1);
+    k_legendre_values<<<grid, 128, 0, s>>>(T, mu, nmu, out);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- GEMM tables
+
+// Byte address, inside a group's table, of element (col, r) of plane `plane`
+// in the tensor-core layout: per (column tile, reduction chunk) one image of
+// 2 planes x nt rows x 128 bytes, rows grouped by 8 into 1024-byte atoms with
+// the 16-byte chunks of row i XOR-permuted by (i mod 8) (the 128-byte
+// swizzle the tensor-core shared-memory descriptor expects for K-major data).
+__device__ inline size_t tc_table_byte(const LegGroup &g, int col, int r, int plane, int es, int kc_len)
+{
+    int ct = col / g.nt, rr = col - ct * g.nt;
+    int kc = r / kc_len, kk = r - kc * kc_len;
+    size_t img = (size_t)g.tab_off + ((size_t)(ct * g.nkc + kc) * 2 + plane) * (size_t)g.nt * 128;
+    int byte = kk * es;
+    return img + (size_t)(rr >> 3) * 1024 + (size_t)(rr & 7) * 128 +
+           (size_t)((((byte >> 4) ^ (rr & 7)) << 4) | (byte & 15));
+}
+
+__device__ inline float round_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int PREC>
+__device__ inline void put_table(void *tab, const LegGroup &g, int col, int r, double v)
+{
+    if (PREC == P_FP64) {
+        ((double *)tab)[g.tab_off + (long long)col * g.K + r] = v;
+    } else if (PREC == P_FP32) {
+        ((float *)tab)[g.tab_off + (long long)col * g.K + r] = (float)v;
+    } else if (PREC == P_TF32X3) {
+        float hi = round_tf32((float)v);
+        float lo = round_tf32((float)(v - (double)hi));
+        char *b = (char *)tab;
+        *(float *)(b + tc_table_byte(g, col, r, 0, 4, 32)) = hi;
+        *(float *)(b + tc_table_byte(g, col, r, 1, 4, 32)) = lo;
+    } else {
+        __nv_bfloat16 hi = __double2bfloat16(v);
+        __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+        char *b = (char *)tab;
+        *(__nv_bfloat16 *)(b + tc_table_byte(g, col, r, 0, 2, 64)) = hi;
+        *(__nv_bfloat16 *)(b + tc_table_byte(g, col, r, 1, 2, 64)) = lo;
+    }
+}
+
+// One thread per (m, northern row j): the inverse table gets Pbar_n^m(mu_j)
+// at (col j, r k), the direct table w_j Pbar_n^m(mu_j) at (col k, r j), with
+// n = m + p + 2k.  Rows that do not keep m (m > M_j) get zeros.
+template <int PREC>
+__global__ void k_tables(int T, int J, int max_m, const double *mu, const double *w, const int *Mrow,
+                         const LegGroup *ginv, const LegGroup *gdir, void *tab_inv, void *tab_dir)
+{
+    int m = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J || m > max_m) return;
+    bool keep = m <= Mrow[j];
+    double x = mu[j], wj = w[j];
+    LegGroup gi[2] = {ginv[2 * m], ginv[2 * m + 1]};
+    LegGroup gd[2] = {gdir[2 * m], gdir[2 * m + 1]};
+    pbar_column(T, m, x, [&](int n, double v) {
+        int p = (n - m) & 1, k = (n - m) >> 1;
+        if (!keep) v = 0.0;
+        if (gi[p].K > 0) put_table<PREC>(tab_inv, gi[p], j, k, v);
+        if (gd[p].ncol > 0) put_table<PREC>(tab_dir, gd[p], k, j, wj * v);
+    });
+}
+
+st_status launch_tables(st_plan *p, cudaStream_t s)
+{
+    int *Mrow_d = nullptr;
+    ST_CUDA(cudaMallocAsync(&Mrow_d, sizeof(int) * p->J, s));
+    ST_CUDA(cudaMemcpyAsync(Mrow_d, p->Mrow.data(), sizeof(int) * p->J, cudaMemcpyHostToDevice, s));
+    dim3 grid((p->J + 63) / 64, p->max_m + 1);
+    switch (p->prec) {
+    case P_FP64:
+        k_tables<P_FP64><<<grid, 64, 0, s>>>(p->T, p->J, p->max_m, p->mu, p->w, Mrow_d, p->groups[0],
+                                             p->groups[1], p->tab[0], p->tab[1]);
+        break;
+    case P_FP32:
+        k_tables<P_FP32><<<grid, 64, 0, s>>>(p->T, p->J, p->max_m, p->mu, p->w, Mrow_d, p->groups[0],
+                                             p->groups[1], p->tab[0], p->tab[1]);
+        break;
+    case P_TF32X3:
+        k_tables<P_TF32X3><<<grid, 64, 0, s>>>(p->T, p->J, p->max_m, p->mu, p->w, Mrow_d, p->groups[0],
+                                               p->groups[1], p->tab[0], p->tab[1]);
+        break;
+    default:
+        k_tables<P_BF16X3><<<grid, 64, 0, s>>>(p->T, p->J, p->max_m, p->mu, p->w, Mrow_d, p->groups[0],
+                                               p->groups[1], p->tab[0], p->tab[1]);
+        break;
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(Mrow_d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_tables");
+    return ST_OK;
+}
+
+// ---------------------------------------------------------------- FFT roots
+
+template <typename C>
+__global__ void k_twiddles(const RowPair *rp, int J, C *tw)
+{
+    int j = blockIdx.y;
+    if (j >= J) return;
+    RowPair r = rp[j];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r.N; t += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)t / (double)r.N, &sn, &cs);
+        C v;
+        v.x = cs;
+        v.y = -sn;
+        tw[r.tw_off + t] = v;
+    }
+}
+
+st_status launch_twiddles(st_plan *p, cudaStream_t s)
+{
+    dim3 grid((p->max_row + 255) / 256, p->J);
+    if (p->prec == P_FP64)
+        k_twiddles<double2><<<grid, 256, 0, s>>>(p->rowpairs, p->J, (double2 *)p->tw);
+    else
+        k_twiddles<float2><<<grid, 256, 0, s>>>(p->rowpairs, p->J, (float2 *)p->tw);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+}  // namespace st
