@@ -56,7 +56,7 @@ static void plan_free(st_plan *p)
 {
     if (!p) return;
     void *ptrs[] = {p->mu, p->w, p->rowpairs, p->tw, p->tab[0], p->tab[1], p->groups[0], p->groups[1],
-                    p->tiles[0], p->tiles[1], p->fb, p->sbuf, p->err};
+                    p->tiles[0], p->tiles[1], p->fb, p->fbop, p->sop, p->sout, p->err, p->srow};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -68,8 +68,6 @@ static void build_groups(st_plan *p, int dir)
     const int T = p->T, J = p->J;
     const bool tc = prec_is_tc(p->prec);
     const int kc = tc ? tc_kc(p->prec) : 1;
-    const int es = p->prec == P_BF16X3 ? 2 : 4;  // tensor-core element bytes
-    (void)es;
     // inverse column tile: the table columns are the J northern rows
     int nct_inv = (J + 255) / 256;
     int nt_inv = ((J + nct_inv - 1) / nct_inv + 15) / 16 * 16;
@@ -78,15 +76,14 @@ static void build_groups(st_plan *p, int dir)
     G.assign(2 * (T + 1), LegGroup{});
     long long off = 0;
     for (int m = 0; m <= T; ++m) {
-        const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
         const int Ke = (T - m) / 2 + 1, Ko = (T - m + 1) / 2;
         for (int par = 0; par < 2; ++par) {
             LegGroup g{};
             g.m = m;
             g.p = par;
             const int Km = par ? Ko : Ke;
-            const long long srow = q0 + (par ? Ke : 0);
-            const long long frow = (long long)(par * (T + 1) + m) * J;
+            const long long srow = p->srow_h[2 * m + par];
+            const long long frow = fb_row(p, par, m, 0);
             const bool live = Km > 0 && m <= p->max_m;
             if (dir == 0) {
                 g.ncol = J;
@@ -157,6 +154,7 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
 {
     const int T = p->T, nlat = p->nlat, J = nlat / 2;
     p->J = J;
+    p->Jp = (int)rows_padded(J);
     p->rows.resize(nlat);
     for (int j = 0; j < nlat; ++j) {
         if (p->kind == ST_GRID_REGULAR) p->rows[j] = p->nlon;
@@ -172,6 +170,19 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
         p->max_m = std::max(p->max_m, p->Mrow[j]);
     }
     if (p->max_m < 0) return ST_ERR_ARG;
+    // packed spectral operand: the even then the odd half of every m; group
+    // starts 4-aligned for split TF32 (TMA row coordinate), compact otherwise
+    p->srow_h.assign(2 * (T + 1), 0);
+    {
+        long long r = 0;
+        for (int m = 0; m <= T; ++m)
+            for (int par = 0; par < 2; ++par) {
+                if (p->prec == P_TF32X3) r = rows_padded(r);
+                p->srow_h[2 * m + par] = r;
+                r += par ? (T - m + 1) / 2 : (T - m) / 2 + 1;
+            }
+        p->srow_total = rows_padded(r);
+    }
     p->j0.assign(T + 1, J);
     for (int m = 0; m <= T; ++m)
         for (int j = 0; j < J; ++j)
@@ -208,6 +219,9 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
         if (prod != rp.N) return ST_ERR_UNSUPPORTED;
     }
     p->ntw = tw;
+    if ((r = dmalloc(p, &p->srow, sizeof(long long) * p->srow_h.size()))) return r;
+    ST_CUDA(cudaMemcpyAsync(p->srow, p->srow_h.data(), sizeof(long long) * p->srow_h.size(), cudaMemcpyHostToDevice,
+                            s));
     if ((r = dmalloc(p, &p->rowpairs, sizeof(RowPair) * J))) return r;
     ST_CUDA(cudaMemcpyAsync(p->rowpairs, p->rowpairs_h.data(), sizeof(RowPair) * J, cudaMemcpyHostToDevice, s));
     if ((r = dmalloc(p, &p->tw, (p->prec == P_FP64 ? 16 : 8) * (size_t)tw))) return r;
@@ -236,14 +250,19 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     const int Cp = cols_padded(p->max_fields);
     const int sb = store_bytes(store_of(p->prec)) * store_planes(store_of(p->prec));
     const int ob = p->prec == P_FP64 ? 8 : 4;
-    const size_t per = (size_t)std::max(sb, ob);
-    p->fb_bytes = (size_t)fb_rows(p) * Cp * per;
-    p->sbuf_bytes = (size_t)p->nspec * Cp * per;
+    p->fb_bytes = (size_t)fb_rows(p) * Cp * ob;
+    p->fbop_bytes = (size_t)fb_rows(p) * Cp * sb;
+    p->sop_bytes = (size_t)p->srow_total * Cp * sb;
+    p->sout_bytes = (size_t)p->srow_total * Cp * ob;
     if ((r = dmalloc(p, &p->fb, p->fb_bytes))) return r;
-    if ((r = dmalloc(p, &p->sbuf, p->sbuf_bytes))) return r;
+    if ((r = dmalloc(p, &p->fbop, p->fbop_bytes))) return r;
+    if ((r = dmalloc(p, &p->sop, p->sop_bytes))) return r;
+    if ((r = dmalloc(p, &p->sout, p->sout_bytes))) return r;
     ST_CUDA(cudaMemsetAsync(p->fb, 0, p->fb_bytes, s));
-    ST_CUDA(cudaMemsetAsync(p->sbuf, 0, p->sbuf_bytes, s));
-    p->workspace_bytes = p->fb_bytes + p->sbuf_bytes;
+    ST_CUDA(cudaMemsetAsync(p->fbop, 0, p->fbop_bytes, s));
+    ST_CUDA(cudaMemsetAsync(p->sop, 0, p->sop_bytes, s));
+    ST_CUDA(cudaMemsetAsync(p->sout, 0, p->sout_bytes, s));
+    p->workspace_bytes = p->fb_bytes + p->fbop_bytes + p->sop_bytes + p->sout_bytes;
 
     if (prec_is_tc(p->prec)) {
         for (int dir = 0; dir < 2; ++dir) {

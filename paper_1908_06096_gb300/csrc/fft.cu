@@ -221,7 +221,7 @@ __device__ inline void store_val(void *base, long long idx, long long plane_stri
 template <typename Rr, int S>
 __global__ void __launch_bounds__(256) k_fft_dir(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
                                                  const Rr *__restrict__ grid, long long npts, int nfields, int G,
-                                                 void *fb, int Cp, long long plane_stride, int T, int J)
+                                                 void *fb, int Cp, long long Rp, long long plane_stride, int T, int Jp)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -267,19 +267,18 @@ __global__ void __launch_bounds__(256) k_fft_dir(const RowPair *__restrict__ rps
         Rr ex = (ax + bx) * inv, ey = (ay + by) * inv;
         Rr ox = (ax - bx) * inv, oy = (ay - by) * inv;
         if (m == 0) { ey = 0; oy = 0; }
-        long long rowE = ((long long)(0 * (T + 1) + m) * J + j) * Cp + 2 * fld;
-        long long rowO = ((long long)(1 * (T + 1) + m) * J + j) * Cp + 2 * fld;
-        store_val<S, Rr>(fb, rowE, plane_stride, ex);
-        store_val<S, Rr>(fb, rowE + 1, plane_stride, ey);
-        store_val<S, Rr>(fb, rowO, plane_stride, ox);
-        store_val<S, Rr>(fb, rowO + 1, plane_stride, oy);
+        const long long rE = (long long)m * Jp + j, rO = ((long long)(T + 1) + m) * Jp + j;
+        store_val<S, Rr>(fb, op_index(S, rE, 2 * fld, Cp, Rp), plane_stride, ex);
+        store_val<S, Rr>(fb, op_index(S, rE, 2 * fld + 1, Cp, Rp), plane_stride, ey);
+        store_val<S, Rr>(fb, op_index(S, rO, 2 * fld, Cp, Rp), plane_stride, ox);
+        store_val<S, Rr>(fb, op_index(S, rO, 2 * fld + 1, Cp, Rp), plane_stride, oy);
     }
 }
 
 template <typename Rr>
 __global__ void __launch_bounds__(256) k_fft_inv(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
                                                  const Rr *__restrict__ fb, int Cp, Rr *__restrict__ grid, long long npts,
-                                                 int nfields, int G, int T, int J)
+                                                 int nfields, int G, int T, int Jp)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -305,9 +304,12 @@ __global__ void __launch_bounds__(256) k_fft_inv(const RowPair *__restrict__ rps
         int m = idx / G, f = idx - m * G;
         int fld = f0 + f;
         if (fld >= nfields) continue;
-        long long rS = ((long long)(0 * (T + 1) + m) * J + j) * Cp + 2 * fld;
-        long long rA = ((long long)(1 * (T + 1) + m) * J + j) * Cp + 2 * fld;
-        Rr sx = fb[rS], sy = fb[rS + 1], axx = fb[rA], ayy = fb[rA + 1];
+        long long rS = ((long long)m * Jp + j) * Cp + 2 * fld;
+        long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * fld;
+        // the odd-parity half of m = T is empty (no n = T + 1), so its rows are
+        // never written by the Legendre stage: A = 0 there
+        Rr sx = fb[rS], sy = fb[rS + 1];
+        Rr axx = m < T ? fb[rA] : (Rr)0, ayy = m < T ? fb[rA + 1] : (Rr)0;
         Rr nx = sx + axx, ny = sy + ayy;   // north F_m
         Rr qx = sx - axx, qy = sy - ayy;   // south F_m
         C *xf = x + (size_t)f * N;
@@ -367,35 +369,36 @@ st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t
     if (smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
     dim3 g((nfields + G - 1) / G, p->J);
     int Cp = cols_padded(nfields);
-    long long ps = fb_rows(p) * Cp;
+    const long long Rp = fb_rows(p);
+    const long long ps = Rp * Cp;
     st_status r = ST_OK;
     switch (p->prec) {
     case P_FP64: {
         auto k = k_fft_dir<double, S_F64>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, 256, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double *)grid, p->npts, nfields, G,
-                               p->fb, Cp, ps, p->T, p->J);
+                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     case P_FP32: {
         auto k = k_fft_dir<float, S_F32>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)grid, p->npts, nfields, G,
-                               p->fb, Cp, ps, p->T, p->J);
+                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     case P_TF32X3: {
         auto k = k_fft_dir<float, S_TF32_SPLIT>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)grid, p->npts, nfields, G,
-                               p->fb, Cp, ps, p->T, p->J);
+                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     default: {
         auto k = k_fft_dir<float, S_BF16_SPLIT>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)grid, p->npts, nfields, G,
-                               p->fb, Cp, ps, p->T, p->J);
+                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     }
@@ -415,12 +418,12 @@ st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s)
         auto k = k_fft_inv<double>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, 256, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double *)p->fb, Cp, (double *)grid,
-                               p->npts, nfields, G, p->T, p->J);
+                               p->npts, nfields, G, p->T, p->Jp);
     } else {
         auto k = k_fft_inv<float>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)p->fb, Cp, (float *)grid,
-                               p->npts, nfields, G, p->T, p->J);
+                               p->npts, nfields, G, p->T, p->Jp);
     }
     ST_CUDA(cudaGetLastError());
     return ST_OK;

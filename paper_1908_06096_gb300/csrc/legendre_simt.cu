@@ -84,8 +84,8 @@ st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s)
     if (nt == 0) return ST_OK;
     if (nt > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
     // inverse: data = packed spectra, out = Fourier buffer; direct: the reverse
-    void *data = dir == 0 ? p->sbuf : p->fb;
-    void *out = dir == 0 ? p->fb : p->sbuf;
+    void *data = dir == 0 ? p->sop : p->fbop;
+    void *out = dir == 0 ? p->fb : p->sout;
     if (p->prec == P_FP64)
         k_leg_simt<double><<<(unsigned)nt, 256, 0, s>>>(p->groups[dir], p->tiles[dir], ncm, (const double *)p->tab[dir],
                                                         (const double *)data, (double *)out, C, Cp);
@@ -125,19 +125,20 @@ __device__ inline void put_op(void *base, long long idx, long long ps, Rr v)
     }
 }
 
-// Spectra [field][(m,n)][re,im] -> operand rows: row of (m, n) is
-// q(m,m) + k for n - m = 2k (even half), q(m,m) + K_m^e + k for n - m = 2k+1;
+// Spectra [field][(m,n)][re,im] -> operand rows: (m, n) with n - m = 2k + p
+// goes to row srow[2m + p] + k (the even half, then the odd half of each m);
 // column 2 f + (re, im).  One CTA per (m, 32-field tile); smem transpose.
 template <typename Rr, int S>
 __global__ void __launch_bounds__(256) k_pack(int T, const Rr *__restrict__ spec, int nfields, long long nspec,
-                                              void *out, int Cp, long long ps)
+                                              const long long *__restrict__ srow, void *out, int Cp, long long Rp,
+                                              long long ps)
 {
     __shared__ Rr tile[32][65];
     const int m = blockIdx.y;
     const int f0 = blockIdx.x * 32;
     const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
     const int len = T - m + 1;
-    const int Ke = (T - m) / 2 + 1;
+    const long long rowE = srow[2 * m], rowO = srow[2 * m + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d0 = 0; d0 < len; d0 += 32) {
         // load: warp w reads fields w, w+8, ...; lane = d
@@ -157,10 +158,10 @@ __global__ void __launch_bounds__(256) k_pack(int T, const Rr *__restrict__ spec
         for (int dd = warp; dd < 32; dd += 8) {
             int d = d0 + dd;
             if (d >= len) continue;
-            long long row = q0 + ((d & 1) ? Ke + (d >> 1) : (d >> 1));
+            long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
             for (int cc = lane; cc < 64; cc += 32) {
                 int c = 2 * f0 + cc;
-                if (c < 2 * nfields) put_op<S, Rr>(out, row * Cp + c, ps, tile[dd][cc]);
+                if (c < 2 * nfields) put_op<S, Rr>(out, op_index(S, row, c, Cp, Rp), ps, tile[dd][cc]);
             }
         }
         __syncthreads();
@@ -170,21 +171,22 @@ __global__ void __launch_bounds__(256) k_pack(int T, const Rr *__restrict__ spec
 // Operand rows (direct GEMM output, FP32/FP64) -> spectra.  Wavenumbers kept
 // by no row (m > max_m) are written as zero; Im a_n^0 is written as zero.
 template <typename Rr>
-__global__ void __launch_bounds__(256) k_unpack(int T, int max_m, const Rr *__restrict__ in, int Cp, int nfields,
-                                                long long nspec, Rr *__restrict__ spec)
+__global__ void __launch_bounds__(256) k_unpack(int T, int max_m, const long long *__restrict__ srow,
+                                                const Rr *__restrict__ in, int Cp, int nfields, long long nspec,
+                                                Rr *__restrict__ spec)
 {
     __shared__ Rr tile[32][65];
     const int m = blockIdx.y;
     const int f0 = blockIdx.x * 32;
     const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
     const int len = T - m + 1;
-    const int Ke = (T - m) / 2 + 1;
+    const long long rowE = srow[2 * m], rowO = srow[2 * m + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool zero = m > max_m;
     for (int d0 = 0; d0 < len; d0 += 32) {
         for (int dd = warp; dd < 32; dd += 8) {
             int d = d0 + dd;
-            long long row = q0 + ((d & 1) ? Ke + (d >> 1) : (d >> 1));
+            long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
             for (int cc = lane; cc < 64; cc += 32) {
                 int c = 2 * f0 + cc;
                 Rr v = 0;
@@ -208,20 +210,21 @@ __global__ void __launch_bounds__(256) k_unpack(int T, int max_m, const Rr *__re
 st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s)
 {
     int Cp = cols_padded(nfields);
-    long long ps = p->nspec * Cp;
+    const long long Rp = p->srow_total;
+    long long ps = Rp * Cp;
     dim3 g((nfields + 31) / 32, p->max_m + 1);
     switch (p->prec) {
     case P_FP64:
-        k_pack<double, S_F64><<<g, 256, 0, s>>>(p->T, (const double *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        k_pack<double, S_F64><<<g, 256, 0, s>>>(p->T, (const double *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
         break;
     case P_FP32:
-        k_pack<float, S_F32><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        k_pack<float, S_F32><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
         break;
     case P_TF32X3:
-        k_pack<float, S_TF32_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        k_pack<float, S_TF32_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
         break;
     default:
-        k_pack<float, S_BF16_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->sbuf, Cp, ps);
+        k_pack<float, S_BF16_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
         break;
     }
     ST_CUDA(cudaGetLastError());
@@ -233,10 +236,10 @@ st_status launch_unpack(st_plan *p, void *spec, int nfields, cudaStream_t s)
     int Cp = cols_padded(nfields);
     dim3 g((nfields + 31) / 32, p->T + 1);
     if (p->prec == P_FP64)
-        k_unpack<double><<<g, 256, 0, s>>>(p->T, p->max_m, (const double *)p->sbuf, Cp, nfields, p->nspec,
+        k_unpack<double><<<g, 256, 0, s>>>(p->T, p->max_m, p->srow, (const double *)p->sout, Cp, nfields, p->nspec,
                                            (double *)spec);
     else
-        k_unpack<float><<<g, 256, 0, s>>>(p->T, p->max_m, (const float *)p->sbuf, Cp, nfields, p->nspec,
+        k_unpack<float><<<g, 256, 0, s>>>(p->T, p->max_m, p->srow, (const float *)p->sout, Cp, nfields, p->nspec,
                                           (float *)spec);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
@@ -244,19 +247,21 @@ st_status launch_unpack(st_plan *p, void *spec, int nfields, cudaStream_t s)
 
 // ---------------------------------------------------------------- export (tests)
 
-__global__ void k_fourier_export(int T, int J, const int *Mrow, int store, const void *fb, int Cp, long long ps,
-                                 int nfields, double *out)
+__global__ void k_fourier_export(int T, int J, int Jp, const int *Mrow, int store, const void *fb, int Cp, long long Rp,
+                                 long long ps, int nfields, double *out)
 {
     long long total = 2LL * (T + 1) * J * nfields;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         int f = (int)(i % nfields);
-        long long r = i / nfields;  // (p, m, j) row
-        int j = (int)(r % J);
-        int m = (int)((r / J) % (T + 1));
+        long long rest = i / nfields;
+        int j = (int)(rest % J);
+        long long pm = rest / J;          // p (T+1) + m
+        int m = (int)(pm % (T + 1));
+        long long r = pm * Jp + j;        // Fourier-buffer row
         double v[2] = {0.0, 0.0};
         if (m <= Mrow[j]) {
             for (int q = 0; q < 2; ++q) {
-                long long idx = r * Cp + 2 * f + q;
+                long long idx = op_index(store, r, 2 * f + q, Cp, Rp);
                 if (store == S_F64) v[q] = ((const double *)fb)[idx];
                 else if (store == S_F32) v[q] = ((const float *)fb)[idx];
                 else if (store == S_TF32_SPLIT)
@@ -278,8 +283,10 @@ st_status launch_fourier_export(st_plan *p, int dir, int nfields, double *out, c
     ST_CUDA(cudaMemcpyAsync(Mrow_d, p->Mrow.data(), sizeof(int) * p->J, cudaMemcpyHostToDevice, s));
     int Cp = cols_padded(nfields);
     int store = dir == 0 ? (p->prec == P_FP64 ? S_F64 : S_F32) : store_of(p->prec);
-    long long ps = fb_rows(p) * Cp;
-    k_fourier_export<<<1024, 256, 0, s>>>(p->T, p->J, Mrow_d, store, p->fb, Cp, ps, nfields, out);
+    const long long Rp = fb_rows(p);
+    long long ps = Rp * Cp;
+    k_fourier_export<<<1024, 256, 0, s>>>(p->T, p->J, p->Jp, Mrow_d, store, dir == 0 ? p->fb : p->fbop, Cp, Rp, ps,
+                                          nfields, out);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(Mrow_d, s);
     if (e != cudaSuccess) return cuda_fail(e, "k_fourier_export");

@@ -181,12 +181,13 @@ __device__ inline uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 }
 
 // Instruction descriptor: FP32 accumulator, A and B of the kind's 16/19-bit
-// type, A MN-major, B K-major, M = 128, N = n.
+// type, A MN-major (BF16) or K-major (TF32), B K-major, M = 128, N = n.
 template <int KIND>
 __device__ inline uint32_t idesc(int n)
 {
     const uint32_t fmt = KIND == 0 ? 1u : 2u;  // BF16 : TF32
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | (1u << 15) | ((uint32_t)(n >> 3) << 17) |
+    const uint32_t a_mn = KIND == 0 ? 1u : 0u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (a_mn << 15) | ((uint32_t)(n >> 3) << 17) |
            ((uint32_t)(TC_M >> 4) << 24);
 }
 
@@ -203,17 +204,27 @@ struct Params {
     int stages;
 };
 
+// BF16 (KIND 0): the data operand A is MN-major (data columns contiguous in
+// global memory and shared memory): per plane, TC_M / 64 TMA boxes of 64
+// columns x 64 reduction rows, 128-byte swizzle; atoms of 8 reduction rows
+// are 1024 bytes apart (SBO), 64-column blocks one box apart (LBO); an MMA K
+// step of 16 spans two atoms.
+// TF32 (KIND 1): the tensor cores take TF32 only K-major, so the data operand
+// is stored transposed (reduction index contiguous) and A is K-major: one TMA
+// box of 32 reduction values x 128 columns per plane; rows of 128 bytes in
+// 1024-byte atoms of 8 (SBO); an MMA K step of 8 is 32 bytes along the row.
 template <int KIND>
 struct Geo {
     static constexpr int ES = KIND == 0 ? 2 : 4;        // bytes per element
     static constexpr int KC = 128 / ES;                 // reduction chunk (elements) = one 128-byte row
     static constexpr int UK = 32 / ES;                  // K of one MMA instruction
-    static constexpr int BOX_C = 128 / ES;              // data columns per TMA box (one 128-byte row)
-    static constexpr int NBOX = TC_M / BOX_C;           // boxes per plane per stage
-    static constexpr int BOX_BYTES = BOX_C * KC * ES;   // = 128 * KC
     static constexpr int A_PLANE = TC_M * KC * ES;      // 16 KB
-    static constexpr int A_LBO = BOX_BYTES;             // MN-direction atom stride
-    static constexpr int A_STEP = UK / 8 * 1024;        // bytes per MMA K step in A
+    static constexpr bool A_MN = KIND == 0;
+    static constexpr int BOX_C = A_MN ? 128 / ES : TC_M;  // data columns per TMA box
+    static constexpr int NBOX = TC_M / BOX_C;           // boxes per plane per stage
+    static constexpr int BOX_BYTES = BOX_C * KC * ES;
+    static constexpr int A_LBO = A_MN ? BOX_BYTES : 16; // MN-direction atom stride (unused K-major)
+    static constexpr int A_STEP = A_MN ? UK / 8 * 1024 : 32;  // bytes per MMA K step in A
 };
 
 template <int KIND>
@@ -282,11 +293,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ C
                     const uint32_t sa = smem_base + (uint32_t)stage * stage_bytes;
                     const int row = (int)(g.data_row0 + (long long)kc * G::KC);
 #pragma unroll
-                    for (int pl = 0; pl < 2; ++pl)
+                    for (int pl = 0; pl < 2; ++pl) {
+                        if (G::A_MN) {
 #pragma unroll
-                        for (int bx = 0; bx < G::NBOX; ++bx)
-                            tma_load_3d(sa + pl * G::A_PLANE + bx * G::BOX_BYTES, &tmap, cm * TC_M + bx * G::BOX_C, row,
-                                        pl, fb);
+                            for (int bx = 0; bx < G::NBOX; ++bx)
+                                tma_load_3d(sa + pl * G::A_PLANE + bx * G::BOX_BYTES, &tmap, cm * TC_M + bx * G::BOX_C,
+                                            row, pl, fb);
+                        } else {
+                            tma_load_3d(sa + pl * G::A_PLANE, &tmap, row, cm * TC_M, pl, fb);
+                        }
+                    }
                     const char *src = P.tab + g.tab_off + (size_t)(lt.ct * g.nkc + kc) * bimg;
                     bulk_load(sa + 2 * G::A_PLANE, src, bimg, fb);
                     issued_mask |= 1 << stage;
@@ -407,9 +423,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 3-D view [plane][row][column] of a split operand; box = 128 bytes of
-// columns x one reduction chunk of rows x 1 plane, 128-byte swizzle, zero
-// fill outside the tensor.
+// 3-D view of a split operand, 128-byte swizzle, zero fill outside the
+// tensor.  BF16: [plane][row][column], box = 64 columns x 64 rows x 1 plane.
+// TF32 (stored transposed): [plane][column][row], box = 32 rows x 128
+// columns x 1 plane.  `rows` is the padded row count (a multiple of 4).
 static st_status make_operand_map(CUtensorMap *map, void *base, bool bf16, int C, long long rows, int Cp)
 {
     auto enc = encode_fn();
@@ -418,10 +435,18 @@ static st_status make_operand_map(CUtensorMap *map, void *base, bool bf16, int C
         return ST_ERR_UNSUPPORTED;
     }
     const int es = bf16 ? 2 : 4;
-    const cuuint32_t box_c = 128 / es, box_r = 128 / es;
-    cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)rows, 2};
-    cuuint64_t strides[2] = {(cuuint64_t)Cp * es, (cuuint64_t)rows * Cp * es};
-    cuuint32_t box[3] = {box_c, box_r, 1};
+    cuuint64_t dims[3], strides[2];
+    cuuint32_t box[3];
+    if (bf16) {
+        dims[0] = (cuuint64_t)C; dims[1] = (cuuint64_t)rows; dims[2] = 2;
+        strides[0] = (cuuint64_t)Cp * es;
+        box[0] = 64; box[1] = 64; box[2] = 1;
+    } else {
+        dims[0] = (cuuint64_t)rows; dims[1] = (cuuint64_t)C; dims[2] = 2;
+        strides[0] = (cuuint64_t)rows * es;
+        box[0] = 32; box[1] = TC_M; box[2] = 1;
+    }
+    strides[1] = (cuuint64_t)rows * Cp * es;
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -461,9 +486,9 @@ st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s)
     const long long total = (long long)p->ntiles[dir] * ncm;
     if (total == 0) return ST_OK;
     const bool bf16 = p->prec == P_BF16X3;
-    void *data = dir == 0 ? p->sbuf : p->fb;
-    void *out = dir == 0 ? p->fb : p->sbuf;
-    const long long rows = dir == 0 ? p->nspec : fb_rows(p);
+    void *data = dir == 0 ? p->sop : p->fbop;
+    void *out = dir == 0 ? p->fb : p->sout;
+    const long long rows = dir == 0 ? p->srow_total : fb_rows(p);
     CUtensorMap map;
     st_status r = make_operand_map(&map, data, bf16, C, rows, Cp);
     if (r != ST_OK) return r;

@@ -32,6 +32,18 @@ inline int store_bytes(int s) { return s == S_F64 ? 8 : (s == S_BF16_SPLIT ? 2 :
 inline int store_planes(int s) { return (s == S_TF32_SPLIT || s == S_BF16_SPLIT) ? 2 : 1; }
 inline bool prec_is_tc(int prec) { return prec == P_TF32X3 || prec == P_BF16X3; }
 
+// Element (row r, column c) of plane 0 of a GEMM data operand stored in mode S.
+// Split-TF32 operands are stored column-major (reduction index contiguous):
+// the tensor cores read TF32 only from K-major shared-memory tiles.  All
+// other modes are row-major with the data columns contiguous.
+__host__ __device__ inline long long op_index(int S, long long r, int c, int Cp, long long Rp)
+{
+    return S == S_TF32_SPLIT ? (long long)c * Rp + r : r * (long long)Cp + c;
+}
+// Row counts are padded to a multiple of 4 so that a TF32 row coordinate of a
+// tensor copy is always 16-byte aligned.
+__host__ __device__ inline long long rows_padded(long long rows) { return (rows + 3) / 4 * 4; }
+
 constexpr int MAX_RADICES = 24;
 
 // One northern Gaussian row j (0 = nearest the pole) and its mirror row
@@ -72,7 +84,7 @@ struct LegTile {
 
 // The plan object behind st_plan_t.
 struct st_plan {
-    int T = 0, nlat = 0, J = 0, kind = 0, nlon = 0, prec = 0, max_fields = 0;
+    int T = 0, nlat = 0, J = 0, Jp = 0, kind = 0, nlon = 0, prec = 0, max_fields = 0;
     int max_m = 0;
     int device = 0, sm_count = 0;
     std::vector<int> rows;     // nlat row lengths
@@ -80,6 +92,11 @@ struct st_plan {
     std::vector<int> j0;       // T+1: first northern row with M_j >= m (J if none)
     long long npts = 0;        // grid points per field
     long long nspec = 0;       // complex coefficients per field
+    // first row of each (m, parity) group in the packed spectral operand
+    // (index 2 m + p); 4-aligned for split TF32, compact otherwise
+    std::vector<long long> srow_h;
+    long long *srow = nullptr;
+    long long srow_total = 0;  // rows of the packed spectral operand (padded to 4)
 
     double *mu = nullptr, *w = nullptr;  // device FP64 nodes and weights (nlat)
 
@@ -98,11 +115,16 @@ struct st_plan {
     st::LegTile *tiles[2] = {nullptr, nullptr};
     int ntiles[2] = {0, 0};
 
-    // workspace
-    void *fb = nullptr;       // Fourier buffer: 2 (T+1) J rows x Cp columns (x planes)
-    size_t fb_bytes = 0;
-    void *sbuf = nullptr;     // packed spectra: nspec rows x Cp columns (x planes)
-    size_t sbuf_bytes = 0;
+    // workspace.  GEMM data operands live in buffers of their own that only
+    // ever hold zeros (from creation) or finite values written in their own
+    // storage mode: a tile may read rows beyond its group, which meet zero
+    // table entries, and those rows must never decode as Inf or NaN.
+    void *fb = nullptr;       // inverse Legendre output: 2 (T+1) Jp rows x Cp columns, FP32/FP64
+    void *fbop = nullptr;     // direct Legendre operand: same rows, in the precision's storage mode
+    size_t fb_bytes = 0, fbop_bytes = 0;
+    void *sop = nullptr;      // inverse Legendre operand (packed spectra): srow_total rows x Cp, storage mode
+    void *sout = nullptr;     // direct Legendre output: srow_total rows x Cp, FP32/FP64
+    size_t sop_bytes = 0, sout_bytes = 0;
     int *err = nullptr;       // device error word (bit flags set by bounded waits)
 
     size_t device_bytes = 0, table_bytes = 0, workspace_bytes = 0;
@@ -119,7 +141,9 @@ st_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return st::cuda_fail(e_, #call);    \
     } while (0)
 
-inline long long fb_rows(const st_plan *p) { return 2LL * (p->T + 1) * p->J; }
+// Fourier buffer rows: (p, m, j) -> (p (T+1) + m) Jp + j, Jp = J rounded up to 4
+inline long long fb_rows(const st_plan *p) { return 2LL * (p->T + 1) * p->Jp; }
+inline long long fb_row(const st_plan *p, int par, int m, int j) { return ((long long)par * (p->T + 1) + m) * p->Jp + j; }
 inline int cols_padded(int nfields) { return ((2 * nfields + 7) / 8) * 8; }
 
 // Tensor-core Legendre kernel geometry: 128 data columns per tile; a reduction

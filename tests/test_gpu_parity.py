@@ -155,23 +155,24 @@ def test_round_trip_fp64_regular_identity(st_mod, oracle_mod):
 
 
 def test_fields_independent_and_reusable_plan(st_mod):
-    """A field's result is the same alone and inside a batch; repeated calls
-    with different field counts on one plan agree."""
+    """A field's result is the same alone and inside a batch (to a few ulps),
+    and repeated calls with different field counts on one plan agree."""
     T = 63
     a = inputs.spectra(T, 40, seed=3)
-    for prec, tol in (("fp64", 0.0), ("bf16x3", 0.0)):
+    for prec, tol in (("fp64", 1e-14), ("bf16x3", 1e-6)):
         dt = torch.float64 if prec == "fp64" else torch.float32
         p = st_mod.Plan(T, "octahedral", precision=prec, max_fields=40)
+        p.inv(_dev(inputs.spectra(T, 40, seed=99), dt))   # leave other data in the workspace
         g_all = p.inv(_dev(a, dt)).clone()
         g_one = p.inv(_dev(a[17:18], dt)).clone()
         g_few = p.inv(_dev(a[15:20], dt)).clone()
-        torch.cuda.synchronize()
-        assert torch.equal(g_all[17], g_one[0])
-        assert torch.equal(g_all[15:20], g_few)
         s_all = p.dir(g_all).clone()
         s_one = p.dir(g_all[17:18].contiguous()).clone()
         torch.cuda.synchronize()
-        assert torch.equal(s_all[17], s_one[0])
+        g_all, g_one, g_few = g_all.cpu().numpy(), g_one.cpu().numpy(), g_few.cpu().numpy()
+        assert max_rel(g_one[0], g_all[17]) <= tol
+        assert max_rel(g_few, g_all[15:20]) <= tol
+        assert max_rel(s_one.cpu().numpy()[0], s_all.cpu().numpy()[17]) <= tol
         p.close()
 
 
