@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Round-trip spherical-harmonic transform benchmark on GB300.
+
+One step = one inverse (spectral -> grid) plus one direct (grid -> spectral)
+transform of every field of the workload, through the C ABI.  The headline
+workload is T639 on the octahedral grid O640 (1280 Gaussian latitudes, row i
+from either pole with 20 + 4 i points, 1 666 560 points per field) with
+137 levels x 4 fields = 548 fields, spectra N(0,1) (n+1)^-1.5, Legendre
+stage in BF16x3 split precision with FP32 accumulation.
+
+Prints one JSON line (rank 0).  `value` is field-transforms/s (fields x
+round trips / s) with inputs resident in HBM; `e2e` is the same with the
+spectra copied host -> device and the result device -> host inside each step.
+`--impl reference` times the FP64 CPU oracle instead (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("field-transforms/s round trip at T639 O1280 x137 lev, split-prec vs FP64 GPU @2e-5; "
+          "p99 latency")
+
+WORKLOADS = {
+    # name: (T, grid, nlat, nlon, fields, spectral decay p, seed)
+    "t639_o640_548": (639, "octahedral", 1280, 0, 548, 1.5, 1002),
+    "t159_reg_411": (159, "regular", 160, 320, 411, 1.0, 1001),
+    "t639_o640_64": (639, "octahedral", 1280, 0, 64, 1.5, 1002),
+    "t31_reg_10": (31, "regular", 32, 64, 10, 1.0, 1000),
+}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def geometry(rows, T):
+    """Per northern row: M_j; per m: first northern row keeping m."""
+    nlat = len(rows)
+    J = nlat // 2
+    M = [min(T, (rows[j] - 1) // 2) for j in range(J)]
+    max_m = max(M)
+    j0 = []
+    for m in range(T + 1):
+        j0.append(next((j for j in range(J) if M[j] >= m), J))
+    return J, M, max_m, j0
+
+
+def algorithmic(T, rows, F, prec):
+    """Algorithmic work of one launch of each kernel for F fields (the counts
+    the roofline fractions divide by)."""
+    J, M, max_m, j0 = geometry(rows, T)
+    npts = sum(rows)
+    nspec = (T + 1) * (T + 2) // 2
+    C = 2 * F
+    # useful Legendre multiply-adds per direction: columns j >= j0(m) (inverse
+    # outputs / direct reduction), all n in [m, T], both parities
+    macs = sum((T - m + 1) * (J - j0[m]) for m in range(max_m + 1)) * C
+    flops = 2.0 * macs
+    split = 3.0 if prec in ("bf16x3", "tf32x3") else 1.0
+    fb_vals = sum(M[j] + 1 for j in range(J)) * 2 * 2 * F  # (E,O or S,A) x (re,im)
+    el = 8 if prec == "fp64" else 4
+    op = {"bf16x3": 4, "tf32x3": 8, "fp32": 4, "fp64": 8}[prec]
+    return {
+        "leg_flops": flops, "leg_tensor_flops": flops * split,
+        "fft_dir_bytes": npts * F * el + fb_vals * op,
+        "fft_inv_bytes": fb_vals * el + npts * F * el,
+        "pack_bytes": nspec * 2 * F * (el + op),
+        "unpack_bytes": nspec * 2 * F * (el + el),
+    }
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle leg
+
+def oracle_round_trip(T, grid, nlat, nlon, spec):
+    import oracle
+    rows = oracle.grid_rows(grid, nlat, nlon)
+    mu, w = oracle.gauss(nlat)
+    t0 = time.perf_counter()
+    g = oracle.inv_trans(T, rows, mu, spec)
+    oracle.dir_trans(T, rows, mu, w, g)
+    return time.perf_counter() - t0, oracle.max_threads()
+
+
+def cpu_baseline(wl, sample_fields=8):
+    from paper_1908_06096_gb300 import inputs
+    T, grid, nlat, nlon, F, p, seed = WORKLOADS[wl]
+    n = min(sample_fields, F)
+    spec = inputs.spectra(T, n, seed=seed, p=p)
+    dt, cores = oracle_round_trip(T, grid, nlat, nlon, spec)
+    return {"value": n / dt, "unit": "field-transforms/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {F} fields of workload {wl}, one round trip (inverse + direct), "
+                      f"{dt:.1f} s; rate per field"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1908_06096_gb300 import inputs
+    wl = args.workload
+    T, grid, nlat, nlon, F, p, seed = WORKLOADS[wl]
+    n = min(args.ref_fields, F)
+    spec = inputs.spectra(T, n, seed=seed, p=p)
+    for _ in range(args.warmup):
+        oracle_round_trip(T, grid, nlat, nlon, spec)
+    times, cores = [], 1
+    for _ in range(args.steps):
+        dt, cores = oracle_round_trip(T, grid, nlat, nlon, spec)
+        times.append(dt)
+    total = sum(times)
+    value = n * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "field-transforms/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, "fp64-oracle"),
+            "cpu_baseline": {"value": value, "unit": "field-transforms/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {n} of {F} fields of workload {wl}, one round trip"},
+            "e2e": {"value": value, "unit": "field-transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, prec):
+    T, grid, nlat, nlon, F, p, seed = WORKLOADS[wl]
+    desc = {"t639_o640_548": "T639 octahedral O640 (1280 Gaussian latitudes, rows 20+4i), 137 levels x 4 fields",
+            "t159_reg_411": "T159 regular 160 x 320 Gaussian grid, 137 levels x 3 fields",
+            "t639_o640_64": "T639 octahedral O640, 64 fields (profiling case)",
+            "t31_reg_10": "T31 regular 32 x 64 Gaussian grid, 10 fields"}[wl]
+    return {"workload": desc, "T": T, "grid": grid, "nlat": nlat, "nlon": nlon or None, "fields": F,
+            "spectra": f"N(0,1) (n+1)^-{p}, seed {seed}", "precision": prec,
+            "step": "inverse + direct transform of every field",
+            "l2": "inputs larger than L2 (no flush needed)" if F >= 64 else "L2 not flushed (small case)"}
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1908_06096_gb300 import inputs, st
+    st.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = args.workload
+    T, grid, nlat, nlon, F, pdec, seed = WORKLOADS[wl]
+    prec = args.precision
+    pk = peaks()
+
+    a = inputs.spectra(T, F, seed=seed + 7919 * rank, p=pdec)
+    plan = st.Plan(T, grid, nlat=nlat, nlon=nlon or None, precision=prec, max_fields=F)
+    dt = plan.dtype
+    spec = torch.from_numpy(a).to(dev, dt)
+    g = torch.empty((F, plan.npts), dtype=dt, device=dev)
+    s_out = torch.empty((F, plan.nspec, 2), dtype=dt, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.inv(spec, out=g)
+        plan.dir(g, out=s_out)
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync()
+    plan.reset_timings()
+    plan.set_timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ck = clocks.stop()
+    plan.set_timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ws, ms)
+    plan.sync()
+    ktimes = plan.timings()
+    value = ws * F / (ms * 1e-3)
+
+    # per-kernel roofline from the in-library events of the timed region
+    rows = plan.row_lengths()
+    alg = algorithmic(T, rows, F, prec)
+    tensor_peak = pk["bf16_tflops_sustained"] * (0.5 if prec == "tf32x3" else 1.0)
+    kern = {}
+    total_k = sum(v["total_ms"] for v in ktimes.values()) or 1.0
+    for name, v in ktimes.items():
+        per = v["total_ms"] / max(v["timed"], 1)
+        e = {"launches": v["launches"], "ms_per_launch": per, "share": v["total_ms"] / total_k}
+        if name.startswith("legendre") and prec in ("bf16x3", "tf32x3"):
+            e.update(bound="tensor", unit="TFLOP/s", achieved=alg["leg_tensor_flops"] / (per * 1e-3) / 1e12,
+                     peak=tensor_peak)
+        elif name.startswith("legendre"):
+            e.update(bound="alu", unit="TFLOP/s", achieved=alg["leg_flops"] / (per * 1e-3) / 1e12, peak=None)
+        else:
+            key = {"fft_direct": "fft_dir_bytes", "fft_inverse": "fft_inv_bytes", "pack_spectra": "pack_bytes",
+                   "unpack_spectra": "unpack_bytes"}.get(name)
+            if key:
+                e.update(bound="hbm", unit="GB/s", achieved=alg[key] / (per * 1e-3) / 1e9, peak=pk["hbm_gbs"])
+        if e.get("peak"):
+            e["frac"] = e["achieved"] / e["peak"]
+        kern[name] = e
+    dom = max(kern, key=lambda k: kern[k]["share"])
+    d = kern[dom]
+    traffic = load_traffic(dom, wl, prec)
+    roof = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"), "peak": d.get("peak"),
+            "unit": d.get("unit"), "frac": d.get("frac"), "traffic": traffic,
+            "peak_source": f"{pk['source']} ({'bf16 sustained' if d.get('unit') == 'TFLOP/s' else 'HBM copy'})"}
+    launches = sum(v["launches"] for v in ktimes.values())
+
+    # end to end through the public API with host buffers
+    h_in = torch.from_numpy(a).to(dt).pin_memory()
+    h_out = torch.empty((F, plan.nspec, 2), dtype=dt).pin_memory()
+    spec_d = torch.empty_like(spec)
+
+    def e2e_step():
+        spec_d.copy_(h_in, non_blocking=True)
+        plan.inv(spec_d, out=g)
+        plan.dir(g, out=s_out)
+        h_out.copy_(s_out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(ws, e0.elapsed_time(e1) / args.steps)
+    nb = F * plan.nspec * 2 * (8 if dt == torch.float64 else 4)
+    e2e = {"value": ws * F / (ms_e2e * 1e-3), "unit": "field-transforms/s", "h2d_bytes_per_step": nb,
+           "d2h_bytes_per_step": nb, "ms_per_step": ms_e2e}
+
+    out = {"metric": METRIC, "value": value, "unit": "field-transforms/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": {"bf16x3": "bf16x3 (fp32 accumulate)", "tf32x3": "tf32x3 (fp32 accumulate)",
+                                           "fp32": "f32", "fp64": "f64"}[prec],
+           "data": "synthetic", "config": config_of(wl, prec), "roofline": roof, "kernels": kern,
+           "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+
+    # other precision forms and the split-precision error against the FP64 GPU form
+    if not args.skip_forms and prec != "fp64":
+        forms = {}
+        res_split = s_out.double().cpu().numpy()
+        del h_in, h_out, spec_d
+        for other in (["tf32x3", "fp64"] if prec == "bf16x3" else ["fp64"]):
+            p2 = st.Plan(T, grid, nlat=nlat, nlon=nlon or None, precision=other, max_fields=F)
+            sp2 = torch.from_numpy(a).to(dev, p2.dtype)
+            g2 = torch.empty((F, p2.npts), dtype=p2.dtype, device=dev)
+            o2 = torch.empty((F, p2.nspec, 2), dtype=p2.dtype, device=dev)
+            nsteps = 2 if other == "fp64" else max(2, args.steps // 2)
+            p2.inv(sp2, out=g2)
+            p2.dir(g2, out=o2)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(nsteps):
+                p2.inv(sp2, out=g2)
+                p2.dir(g2, out=o2)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms2 = e0.elapsed_time(e1) / nsteps
+            forms[other] = {"value": F / (ms2 * 1e-3), "ms_per_step": ms2, "steps": nsteps}
+            if other == "fp64":
+                # errors of the inverse (grid) and the round trip, per field, normwise
+                ref_s = o2.cpu().numpy()
+                gs = g.double()
+                g64 = g2
+                err_grid = per_field(gs, g64)
+                den = np.abs(ref_s).reshape(F, -1).max(axis=1)
+                err_rt = float((np.abs(res_split - ref_s).reshape(F, -1).max(axis=1) / den).max())
+                out["error_vs_fp64_gpu"] = {"grid_max_rel": err_grid, "round_trip_spec_max_rel": err_rt,
+                                            "bar": 2e-5, "metric": "per field max|x - x64| / max|x64|, worst field"}
+            del p2, sp2, g2, o2
+            torch.cuda.empty_cache()
+        forms[prec] = {"value": value, "ms_per_step": ms, "steps": args.steps}
+        out["forms"] = forms
+
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        try:
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_fields)
+        except Exception as ex:  # report, do not hide
+            out["cpu_baseline"] = {"error": repr(ex)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.close()
+
+
+def per_field(x, ref):
+    import torch
+    F = x.shape[0]
+    d = (x - ref).abs().reshape(F, -1).amax(dim=1)
+    r = ref.abs().reshape(F, -1).amax(dim=1)
+    return float((d / r).max().item())
+
+
+def load_traffic(kernel, wl, prec):
+    """dram read+write bytes per launch from the committed ncu summary of this
+    kernel (null if none matches the current build)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get(f"{kernel}|{wl}|{prec}")
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="t639_o640_548", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32", "fp64"])
+    ap.add_argument("--skip-forms", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-fields", type=int, default=8)
+    ap.add_argument("--ref-fields", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -147,6 +147,27 @@ st_status st_dir_trans(st_plan_t plan, const void *grid_dev, void *spec_dev, int
  * recorded since the last call (then clear it). */
 st_status st_plan_sync(st_plan_t plan, void *stream);
 
+/*
+ * Per-kernel timing (not in the paper; a measurement aid).  While enabled,
+ * every kernel the plan launches is bracketed by two CUDA events recorded on
+ * its launch stream; st_plan_timings waits for them and reports, per kernel,
+ * the number of launches and the summed event time since the last reset.
+ * Do not enable timing while capturing the plan's calls into a CUDA graph.
+ * Launch counts are kept whether or not timing is enabled.
+ */
+typedef struct {
+    const char *name;   /* kernel name (static storage) */
+    long long launches; /* launches since the last reset */
+    double total_ms;    /* summed event time of the timed launches */
+    long long timed;    /* launches that were timed */
+} st_kernel_time;
+
+st_status st_plan_set_timing(st_plan_t plan, int enable);
+/* Fill up to `max` entries (one per kernel kind); *n receives the count.
+ * Synchronises on the recorded events. */
+st_status st_plan_timings(st_plan_t plan, st_kernel_time *out, int max, int *n);
+st_status st_plan_reset_timings(st_plan_t plan);
+
 /* Text for a status code (static storage). */
 const char *st_status_string(st_status s);
 

@@ -59,6 +59,11 @@ static void plan_free(st_plan *p)
                     p->tiles[0], p->tiles[1], p->fb, p->fbop, p->sop, p->sout, p->err, p->srow};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    for (auto &e : p->pending) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (auto e : p->event_pool) cudaEventDestroy(e);
     delete p;
 }
 
@@ -288,9 +293,78 @@ static st_status check_fields(st_plan_t p, int nfields)
     return ST_OK;
 }
 
+const char *kernel_name(const st_plan *p, int kind)
+{
+    const bool tc = prec_is_tc(p->prec);
+    switch (kind) {
+    case K_PACK: return "pack_spectra";
+    case K_LEG_INV: return tc ? "legendre_inverse_tcgen05" : "legendre_inverse_simt";
+    case K_FFT_INV: return "fft_inverse";
+    case K_FFT_DIR: return "fft_direct";
+    case K_LEG_DIR: return tc ? "legendre_direct_tcgen05" : "legendre_direct_simt";
+    case K_UNPACK: return "unpack_spectra";
+    case K_EXPORT: return "fourier_export";
+    case K_TABLES: return "plan_tables";
+    }
+    return "?";
+}
+
+static cudaEvent_t take_event(st_plan *p)
+{
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Runs one launcher, counting it and, when timing is on, bracketing it with
+// events on its stream.
+template <class F>
+static st_status counted(st_plan *p, int kind, cudaStream_t s, F f)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (p->timing) {
+        a = take_event(p);
+        b = take_event(p);
+        if (a) cudaEventRecord(a, s);
+    }
+    st_status r = f();
+    if (r == ST_OK) p->launches[kind]++;
+    if (p->timing && a && b) {
+        cudaEventRecord(b, s);
+        p->pending.push_back({kind, a, b});
+    } else {
+        if (a) p->event_pool.push_back(a);
+        if (b) p->event_pool.push_back(b);
+    }
+    return r;
+}
+
 static st_status leg(st_plan *p, int dir, int nfields, cudaStream_t s)
 {
-    return prec_is_tc(p->prec) ? launch_leg_tc(p, dir, nfields, s) : launch_leg_simt(p, dir, nfields, s);
+    return counted(p, dir == 0 ? K_LEG_INV : K_LEG_DIR, s, [&] {
+        return prec_is_tc(p->prec) ? launch_leg_tc(p, dir, nfields, s) : launch_leg_simt(p, dir, nfields, s);
+    });
+}
+static st_status pack(st_plan *p, const void *spec, int nfields, cudaStream_t s)
+{
+    return counted(p, K_PACK, s, [&] { return launch_pack(p, spec, nfields, s); });
+}
+static st_status unpack(st_plan *p, void *spec, int nfields, cudaStream_t s)
+{
+    return counted(p, K_UNPACK, s, [&] { return launch_unpack(p, spec, nfields, s); });
+}
+static st_status fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s)
+{
+    return counted(p, K_FFT_INV, s, [&] { return launch_fft_inv(p, grid, nfields, s); });
+}
+static st_status fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s)
+{
+    return counted(p, K_FFT_DIR, s, [&] { return launch_fft_dir(p, grid, nfields, s); });
 }
 
 }  // namespace st
@@ -400,9 +474,9 @@ st_status st_inv_trans(st_plan_t p, const void *spec_dev, void *grid_dev, int nf
     if (r) return r;
     if (!spec_dev || !grid_dev) return ST_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((r = launch_pack(p, spec_dev, nfields, s))) return r;
+    if ((r = pack(p, spec_dev, nfields, s))) return r;
     if ((r = leg(p, 0, nfields, s))) return r;
-    return launch_fft_inv(p, grid_dev, nfields, s);
+    return fft_inv(p, grid_dev, nfields, s);
 }
 
 st_status st_dir_trans(st_plan_t p, const void *grid_dev, void *spec_dev, int nfields, void *stream)
@@ -411,9 +485,9 @@ st_status st_dir_trans(st_plan_t p, const void *grid_dev, void *spec_dev, int nf
     if (r) return r;
     if (!spec_dev || !grid_dev) return ST_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((r = launch_fft_dir(p, grid_dev, nfields, s))) return r;
+    if ((r = fft_dir(p, grid_dev, nfields, s))) return r;
     if ((r = leg(p, 1, nfields, s))) return r;
-    return launch_unpack(p, spec_dev, nfields, s);
+    return unpack(p, spec_dev, nfields, s);
 }
 
 st_status st_plan_sync(st_plan_t p, void *stream)
@@ -450,7 +524,7 @@ st_status st_inv_legendre(st_plan_t p, const void *spec_dev, int nfields, void *
     if (r) return r;
     if (!spec_dev) return ST_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((r = launch_pack(p, spec_dev, nfields, s))) return r;
+    if ((r = pack(p, spec_dev, nfields, s))) return r;
     return leg(p, 0, nfields, s);
 }
 
@@ -459,7 +533,7 @@ st_status st_inv_fft(st_plan_t p, void *grid_dev, int nfields, void *stream)
     st_status r = check_fields(p, nfields);
     if (r) return r;
     if (!grid_dev) return ST_ERR_ARG;
-    return launch_fft_inv(p, grid_dev, nfields, (cudaStream_t)stream);
+    return fft_inv(p, grid_dev, nfields, (cudaStream_t)stream);
 }
 
 st_status st_dir_fft(st_plan_t p, const void *grid_dev, int nfields, void *stream)
@@ -467,7 +541,7 @@ st_status st_dir_fft(st_plan_t p, const void *grid_dev, int nfields, void *strea
     st_status r = check_fields(p, nfields);
     if (r) return r;
     if (!grid_dev) return ST_ERR_ARG;
-    return launch_fft_dir(p, grid_dev, nfields, (cudaStream_t)stream);
+    return fft_dir(p, grid_dev, nfields, (cudaStream_t)stream);
 }
 
 st_status st_dir_legendre(st_plan_t p, void *spec_dev, int nfields, void *stream)
@@ -477,7 +551,7 @@ st_status st_dir_legendre(st_plan_t p, void *spec_dev, int nfields, void *stream
     if (!spec_dev) return ST_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if ((r = leg(p, 1, nfields, s))) return r;
-    return launch_unpack(p, spec_dev, nfields, s);
+    return unpack(p, spec_dev, nfields, s);
 }
 
 st_status st_fourier_export(st_plan_t p, int direction, int nfields, double *out_dev, void *stream)
@@ -485,7 +559,60 @@ st_status st_fourier_export(st_plan_t p, int direction, int nfields, double *out
     st_status r = check_fields(p, nfields);
     if (r) return r;
     if (!out_dev || direction < 0 || direction > 1) return ST_ERR_ARG;
-    return launch_fourier_export(p, direction, nfields, out_dev, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    return counted(p, K_EXPORT, s, [&] { return launch_fourier_export(p, direction, nfields, out_dev, s); });
+}
+
+st_status st_plan_set_timing(st_plan_t p, int enable)
+{
+    if (!p) return ST_ERR_ARG;
+    p->timing = enable != 0;
+    return ST_OK;
+}
+
+st_status st_plan_timings(st_plan_t p, st_kernel_time *out, int max, int *n)
+{
+    if (!p || (!out && max > 0)) return ST_ERR_ARG;
+    for (auto &e : p->pending) {
+        float ms = 0.f;
+        ST_CUDA(cudaEventSynchronize(e.b));
+        ST_CUDA(cudaEventElapsedTime(&ms, e.a, e.b));
+        p->total_ms[e.kind] += ms;
+        p->timed[e.kind]++;
+        p->event_pool.push_back(e.a);
+        p->event_pool.push_back(e.b);
+    }
+    p->pending.clear();
+    int k = 0;
+    for (int i = 0; i < K_NKINDS; ++i) {
+        if (p->launches[i] == 0) continue;
+        if (k < max) {
+            out[k].name = kernel_name(p, i);
+            out[k].launches = p->launches[i];
+            out[k].total_ms = p->total_ms[i];
+            out[k].timed = p->timed[i];
+        }
+        ++k;
+    }
+    if (n) *n = k;
+    return ST_OK;
+}
+
+st_status st_plan_reset_timings(st_plan_t p)
+{
+    if (!p) return ST_ERR_ARG;
+    for (auto &e : p->pending) {
+        cudaEventSynchronize(e.b);
+        p->event_pool.push_back(e.a);
+        p->event_pool.push_back(e.b);
+    }
+    p->pending.clear();
+    for (int i = 0; i < 16; ++i) {
+        p->launches[i] = 0;
+        p->timed[i] = 0;
+        p->total_ms[i] = 0;
+    }
+    return ST_OK;
 }
 
 }  // extern "C"

@@ -128,6 +128,18 @@ struct st_plan {
     int *err = nullptr;       // device error word (bit flags set by bounded waits)
 
     size_t device_bytes = 0, table_bytes = 0, workspace_bytes = 0;
+
+    // launch accounting and optional event timing, per kernel kind
+    bool timing = false;
+    long long launches[16] = {0};
+    long long timed[16] = {0};
+    double total_ms[16] = {0};
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace st {
@@ -151,6 +163,12 @@ inline int cols_padded(int nfields) { return ((2 * nfields + 7) / 8) * 8; }
 constexpr int TC_M = 128;
 inline int tc_kc(int prec) { return prec == P_BF16X3 ? 64 : 32; }
 constexpr int SIMT_TILE = 64;
+
+// Kernel kinds for launch accounting.
+enum KernelKind {
+    K_PACK = 0, K_LEG_INV, K_FFT_INV, K_FFT_DIR, K_LEG_DIR, K_UNPACK, K_EXPORT, K_TABLES, K_NKINDS
+};
+const char *kernel_name(const st_plan *p, int kind);
 
 // ---- launchers implemented in the .cu files ----
 st_status launch_tables(st_plan *p, cudaStream_t s);

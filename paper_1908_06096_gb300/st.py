@@ -40,6 +40,11 @@ class _PlanInfo(ctypes.Structure):
                 ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t)]
 
 
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double),
+                ("timed", ctypes.c_longlong)]
+
+
 _lib = None
 
 # (name, argtypes) of every exported entry point; the ABI test checks this
@@ -63,6 +68,9 @@ SIGNATURES = {
     "st_dir_fft": [_VP, _VP, _I, _VP],
     "st_dir_legendre": [_VP, _VP, _I, _VP],
     "st_fourier_export": [_VP, _I, _I, _VP, _VP],
+    "st_plan_set_timing": [_VP, _I],
+    "st_plan_timings": [_VP, ctypes.POINTER(_KernelTime), _I, ctypes.POINTER(ctypes.c_int)],
+    "st_plan_reset_timings": [_VP],
 }
 
 
@@ -201,6 +209,20 @@ class Plan:
             out = torch.empty((nf, self.nspec, 2), dtype=self.dtype, device=grid.device)
         _check(load().st_dir_trans(self._h, _ptr(grid), _ptr(out), nf, _stream_handle(stream)), "st_dir_trans")
         return out
+
+    def set_timing(self, enable: bool):
+        _check(load().st_plan_set_timing(self._h, 1 if enable else 0), "st_plan_set_timing")
+
+    def reset_timings(self):
+        _check(load().st_plan_reset_timings(self._h), "st_plan_reset_timings")
+
+    def timings(self) -> dict:
+        """{kernel name: {"launches", "timed", "total_ms"}} since the last reset."""
+        arr = (_KernelTime * 16)()
+        n = ctypes.c_int()
+        _check(load().st_plan_timings(self._h, arr, 16, ctypes.byref(n)), "st_plan_timings")
+        return {arr[i].name.decode(): {"launches": int(arr[i].launches), "timed": int(arr[i].timed),
+                                       "total_ms": float(arr[i].total_ms)} for i in range(min(n.value, 16))}
 
     def sync(self, stream=None):
         _check(load().st_plan_sync(self._h, _stream_handle(stream)), "st_plan_sync")
