@@ -42,6 +42,33 @@ static int factorize(int N, int *rad)
     return n;
 }
 
+// Smallest 2^a 3^b 5^c >= n with a >= 2 (so that radix-4 passes lead).
+static int smooth_at_least(int n)
+{
+    for (int L = std::max(n, 4);; ++L) {
+        if (L % 4) continue;
+        int q = L;
+        while (q % 2 == 0) q /= 2;
+        while (q % 3 == 0) q /= 3;
+        while (q % 5 == 0) q /= 5;
+        if (q == 1) return L;
+    }
+}
+
+// Rough per-field work models (complex multiply-adds) used to pick a row's
+// FFT form: a Stockham pass of radix r costs about N r, a pass over a prime
+// above 5 (one output per thread, table look-ups) about twice that.
+static double direct_cost(int N, const int *rad, int n)
+{
+    double c = 0;
+    for (int q = 0; q < n; ++q) c += (double)N * rad[q] * (rad[q] > 5 ? 2.0 : 1.0);
+    return c;
+}
+static double bluestein_cost(int L, const int *rad, int n)
+{
+    return 2.0 * direct_cost(L, rad, n) + 4.0 * L;
+}
+
 template <typename T>
 static st_status dmalloc(st_plan *p, T **ptr, size_t bytes)
 {
@@ -55,8 +82,8 @@ static st_status dmalloc(st_plan *p, T **ptr, size_t bytes)
 static void plan_free(st_plan *p)
 {
     if (!p) return;
-    void *ptrs[] = {p->mu, p->w, p->rowpairs, p->tw, p->tab[0], p->tab[1], p->groups[0], p->groups[1],
-                    p->tiles[0], p->tiles[1], p->fb, p->fbop, p->sop, p->sout, p->err, p->srow};
+    void *ptrs[] = {p->mu, p->w, p->rowpairs, p->tw, p->chirp, p->kern, p->tab[0], p->tab[1], p->groups[0],
+                    p->groups[1], p->tiles[0], p->tiles[1], p->fb, p->fbop, p->sop, p->sout, p->err, p->srow};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : p->pending) {
@@ -202,35 +229,66 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     if ((r = dmalloc(p, &p->w, sizeof(double) * nlat))) return r;
     if ((r = launch_gauss(nlat, p->mu, p->w, s))) return r;
 
-    // FFT rows
+    // FFT rows: mixed radix over N, or Bluestein over a 5-smooth L >= 2N - 1
+    // where N has a large prime factor and that is cheaper (FP64 plans keep
+    // the direct form: their parity, not their speed, is what they are for)
     p->rowpairs_h.resize(J);
-    long long off = 0, tw = 0;
+    long long off = 0, tw = 0, nch = 0, nkn = 0;
     std::vector<long long> roff(nlat);
     for (int j = 0; j < nlat; ++j) { roff[j] = off; off += p->rows[j]; }
-    p->max_row = 0;
+    p->max_row = p->max_fft = p->max_chirp = 0;
     for (int j = 0; j < J; ++j) {
         RowPair &rp = p->rowpairs_h[j];
         memset(&rp, 0, sizeof(rp));
         rp.N = p->rows[j];
         rp.M = p->Mrow[j];
-        rp.nrad = factorize(rp.N, rp.rad);
+        int radN[MAX_RADICES];
+        int nN = factorize(rp.N, radN);
+        long long prod = 1;
+        for (int q = 0; q < nN; ++q) prod *= radN[q];
+        if (prod != rp.N) return ST_ERR_UNSUPPORTED;
+        const int L = smooth_at_least(2 * rp.N - 1);
+        int radL[MAX_RADICES];
+        int nL = factorize(L, radL);
+        if (p->prec != P_FP64 && bluestein_cost(L, radL, nL) < direct_cost(rp.N, radN, nN)) {
+            rp.mode = 1;
+            rp.fftlen = L;
+            rp.nrad = nL;
+            memcpy(rp.rad, radL, sizeof(int) * nL);
+            rp.chirp_off = nch;
+            rp.kern_off = nkn;
+            nch += rp.N;
+            nkn += L;
+            p->max_chirp = std::max(p->max_chirp, rp.N);
+        } else {
+            rp.mode = 0;
+            rp.fftlen = rp.N;
+            rp.nrad = nN;
+            memcpy(rp.rad, radN, sizeof(int) * nN);
+        }
         rp.tw_off = tw;
+        tw += rp.fftlen;
         rp.off_n = roff[j];
         rp.off_s = roff[nlat - 1 - j];
-        tw += rp.N;
         p->max_row = std::max(p->max_row, rp.N);
-        int prod = 1;
-        for (int q = 0; q < rp.nrad; ++q) prod *= rp.rad[q];
-        if (prod != rp.N) return ST_ERR_UNSUPPORTED;
+        p->max_fft = std::max(p->max_fft, rp.fftlen);
     }
     p->ntw = tw;
+    p->nchirp = nch;
+    p->nkern = nkn;
     if ((r = dmalloc(p, &p->srow, sizeof(long long) * p->srow_h.size()))) return r;
     ST_CUDA(cudaMemcpyAsync(p->srow, p->srow_h.data(), sizeof(long long) * p->srow_h.size(), cudaMemcpyHostToDevice,
                             s));
     if ((r = dmalloc(p, &p->rowpairs, sizeof(RowPair) * J))) return r;
     ST_CUDA(cudaMemcpyAsync(p->rowpairs, p->rowpairs_h.data(), sizeof(RowPair) * J, cudaMemcpyHostToDevice, s));
-    if ((r = dmalloc(p, &p->tw, (p->prec == P_FP64 ? 16 : 8) * (size_t)tw))) return r;
+    const size_t cs = p->prec == P_FP64 ? 16 : 8;
+    if ((r = dmalloc(p, &p->tw, cs * (size_t)tw))) return r;
     if ((r = launch_twiddles(p, s))) return r;
+    if (nch > 0) {
+        if ((r = dmalloc(p, &p->chirp, cs * (size_t)nch))) return r;
+        if ((r = dmalloc(p, &p->kern, cs * (size_t)nkn))) return r;
+        if ((r = launch_bluestein_setup(p, s))) return r;
+    }
 
     // Legendre groups, tiles, tables
     for (int dir = 0; dir < 2; ++dir) {

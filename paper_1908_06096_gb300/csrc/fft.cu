@@ -17,7 +17,11 @@
 // Hermitian spectra -> one complex inverse FFT -> both rows.
 #include "st_internal.cuh"
 
+#include <algorithm>
+
 namespace st {
+
+constexpr int FFT_THREADS = 512;
 
 template <typename R> struct CT;
 template <> struct CT<double> { typedef double2 T; };
@@ -109,14 +113,14 @@ template <typename C> __device__ inline void dft5(C *v)
 // One Stockham pass of radix R (2, 3, 4 or 5) over G sequences of length N in
 // shared memory: src -> dst, L = product of the radices of earlier passes.
 template <int R, typename C>
-__device__ inline void pass_small(const C *src, C *dst, const C *tw, int N, int L, int G)
+__device__ inline void pass_small(const C *src, C *dst, const C *tw, int N, int S, int L, int G)
 {
     int nb = N / R;
     int step = N / (L * R);
     for (int idx = threadIdx.x; idx < G * nb; idx += blockDim.x) {
         int f = idx / nb, b = idx - f * nb;
         int k = b % L, grp = b / L;
-        const C *s = src + (size_t)f * N;
+        const C *s = src + (size_t)f * S;
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = s[b + r * nb];
@@ -128,7 +132,7 @@ __device__ inline void pass_small(const C *src, C *dst, const C *tw, int N, int 
         if (R == 3) dft3(v);
         if (R == 4) dft4(v);
         if (R == 5) dft5(v);
-        C *d = dst + (size_t)f * N + (size_t)grp * L * R + k;
+        C *d = dst + (size_t)f * S + (size_t)grp * L * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) d[r * L] = v[r];
     }
@@ -137,7 +141,7 @@ __device__ inline void pass_small(const C *src, C *dst, const C *tw, int N, int 
 // Stockham pass of any radix R as a direct DFT over the factor, one output
 // per thread: out[grp L R + s L + k] = sum_r src[b + r N/R] W_N^{r (k + s L) N/(L R)}.
 template <typename C>
-__device__ inline void pass_generic(const C *src, C *dst, const C *tw, int N, int L, int R, int G)
+__device__ inline void pass_generic(const C *src, C *dst, const C *tw, int N, int S, int L, int R, int G)
 {
     int nb = N / R;
     int step = N / (L * R);
@@ -147,7 +151,7 @@ __device__ inline void pass_generic(const C *src, C *dst, const C *tw, int N, in
         int s_ = (o / L) % R;
         int grp = o / (L * R);
         int b = grp * L + k;
-        const C *s = src + (size_t)f * N;
+        const C *s = src + (size_t)f * S;
         int e = (k + s_ * L) * step;  // < N
         int ex = 0;
         C acc;
@@ -161,23 +165,25 @@ __device__ inline void pass_generic(const C *src, C *dst, const C *tw, int N, in
             ex += e;
             if (ex >= N) ex -= N;
         }
-        dst[(size_t)f * N + o] = acc;
+        dst[(size_t)f * S + o] = acc;
     }
 }
 
-// Runs all passes; returns the buffer that holds the result.
+// Runs all passes of length n = rp.fftlen over G sequences spaced S apart;
+// returns the buffer that holds the result.
 template <typename C>
-__device__ C *fft_passes(C *x, C *y, const C *tw, const RowPair &rp, int G)
+__device__ C *fft_passes(C *x, C *y, const C *tw, const RowPair &rp, int G, int S)
 {
     int L = 1;
+    const int n = rp.fftlen;
     for (int q = 0; q < rp.nrad; ++q) {
         int R = rp.rad[q];
         switch (R) {
-        case 2: pass_small<2, C>(x, y, tw, rp.N, L, G); break;
-        case 3: pass_small<3, C>(x, y, tw, rp.N, L, G); break;
-        case 4: pass_small<4, C>(x, y, tw, rp.N, L, G); break;
-        case 5: pass_small<5, C>(x, y, tw, rp.N, L, G); break;
-        default: pass_generic<C>(x, y, tw, rp.N, L, R, G); break;
+        case 2: pass_small<2, C>(x, y, tw, n, S, L, G); break;
+        case 3: pass_small<3, C>(x, y, tw, n, S, L, G); break;
+        case 4: pass_small<4, C>(x, y, tw, n, S, L, G); break;
+        case 5: pass_small<5, C>(x, y, tw, n, S, L, G); break;
+        default: pass_generic<C>(x, y, tw, n, S, L, R, G); break;
         }
         __syncthreads();
         C *t = x;
@@ -186,6 +192,52 @@ __device__ C *fft_passes(C *x, C *y, const C *tw, const RowPair &rp, int G)
         L *= R;
     }
     return x;
+}
+
+// Forward N-point DFT of the G sequences in x (each in the first N slots of
+// a stride-S slot); returns the buffer holding Z_0 .. Z_{N-1} per field.
+// Mode 1 (Bluestein): Z_m = w_m conj(FFT_L(conj(FFT_L(z w) * kern)))_m with
+// kern = FFT_L(b) / L, which is the circular convolution with b written
+// through the conjugation identity IFFT(v) = conj(FFT(conj(v))) / L.
+template <typename C>
+__device__ C *fft_forward(C *x, C *y, const C *tw, const C *chirp, const C *__restrict__ kern, const RowPair &rp,
+                          int G, int S)
+{
+    if (rp.mode == 0) return fft_passes<C>(x, y, tw, rp, G, S);
+    const int N = rp.N, L = rp.fftlen;
+    for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
+        int f = idx / L, k = idx - f * L;
+        C *v = x + (size_t)f * S + k;
+        if (k < N) {
+            *v = cmul(*v, chirp[k]);
+        } else {
+            C z;
+            z.x = 0;
+            z.y = 0;
+            *v = z;
+        }
+    }
+    __syncthreads();
+    C *a = fft_passes<C>(x, y, tw, rp, G, S);
+    C *other = a == x ? y : x;
+    for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
+        int f = idx / L, k = idx - f * L;
+        C *v = a + (size_t)f * S + k;
+        C t = cmul(*v, kern[k]);
+        t.y = -t.y;
+        *v = t;
+    }
+    __syncthreads();
+    C *q = fft_passes<C>(a, other, tw, rp, G, S);
+    for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
+        int f = idx / N, m = idx - f * N;
+        C *v = q + (size_t)f * S + m;
+        C t = *v;
+        t.y = -t.y;
+        *v = cmul(chirp[m], t);
+    }
+    __syncthreads();
+    return q;
 }
 
 __device__ inline float round_tf32_f(float x)
@@ -219,21 +271,28 @@ __device__ inline void store_val(void *base, long long idx, long long plane_stri
 }
 
 template <typename Rr, int S>
-__global__ void __launch_bounds__(256) k_fft_dir(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
-                                                 const Rr *__restrict__ grid, long long npts, int nfields, int G,
-                                                 void *fb, int Cp, long long Rp, long long plane_stride, int T, int Jp)
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_dir(const RowPair *__restrict__ rps,
+                                                         const typename CT<Rr>::T *__restrict__ tw_all,
+                                                         const typename CT<Rr>::T *__restrict__ chirp_all,
+                                                         const typename CT<Rr>::T *__restrict__ kern_all,
+                                                         const Rr *__restrict__ grid, long long npts, int nfields, int G,
+                                                         void *fb, int Cp, long long Rp, long long plane_stride, int T,
+                                                         int Jp)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int j = blockIdx.y;
     const RowPair rp = rps[j];
-    const int N = rp.N;
+    const int N = rp.N, W = rp.fftlen;
     C *tw = (C *)smem_raw;
-    C *x = tw + N;
-    C *y = x + (size_t)G * N;
+    C *ch = tw + W;
+    C *x = ch + (rp.mode ? N : 0);
+    C *y = x + (size_t)G * W;
     const int f0 = blockIdx.x * G;
 
-    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = tw_all[rp.tw_off + t];
+    for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = tw_all[rp.tw_off + t];
+    if (rp.mode)
+        for (int t = threadIdx.x; t < N; t += blockDim.x) ch[t] = chirp_all[rp.chirp_off + t];
     for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
         int f = idx / N, k = idx - f * N;
         int fld = f0 + f;
@@ -245,10 +304,10 @@ __global__ void __launch_bounds__(256) k_fft_dir(const RowPair *__restrict__ rps
             v.x = g[rp.off_n + k];
             v.y = g[rp.off_s + k];
         }
-        x[idx] = v;
+        x[(size_t)f * W + k] = v;
     }
     __syncthreads();
-    C *z = fft_passes<C>(x, y, tw, rp, G);
+    C *z = fft_forward<C>(x, y, tw, ch, kern_all + rp.kern_off, rp, G, W);
 
     const Rr inv = (Rr)1.0 / (Rr)N;
     const int M = rp.M;
@@ -256,7 +315,7 @@ __global__ void __launch_bounds__(256) k_fft_dir(const RowPair *__restrict__ rps
         int m = idx / G, f = idx - m * G;
         int fld = f0 + f;
         if (fld >= nfields) continue;
-        const C *zf = z + (size_t)f * N;
+        const C *zf = z + (size_t)f * W;
         C zm = zf[m];
         C zc = zf[m == 0 ? 0 : N - m];
         zc.y = -zc.y;
@@ -276,22 +335,28 @@ __global__ void __launch_bounds__(256) k_fft_dir(const RowPair *__restrict__ rps
 }
 
 template <typename Rr>
-__global__ void __launch_bounds__(256) k_fft_inv(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
-                                                 const Rr *__restrict__ fb, int Cp, Rr *__restrict__ grid, long long npts,
-                                                 int nfields, int G, int T, int Jp)
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_inv(const RowPair *__restrict__ rps,
+                                                         const typename CT<Rr>::T *__restrict__ tw_all,
+                                                         const typename CT<Rr>::T *__restrict__ chirp_all,
+                                                         const typename CT<Rr>::T *__restrict__ kern_all,
+                                                         const Rr *__restrict__ fb, int Cp, Rr *__restrict__ grid,
+                                                         long long npts, int nfields, int G, int T, int Jp)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int j = blockIdx.y;
     const RowPair rp = rps[j];
-    const int N = rp.N;
+    const int N = rp.N, W = rp.fftlen;
     C *tw = (C *)smem_raw;
-    C *x = tw + N;
-    C *y = x + (size_t)G * N;
+    C *ch = tw + W;
+    C *x = ch + (rp.mode ? N : 0);
+    C *y = x + (size_t)G * W;
     const int f0 = blockIdx.x * G;
 
-    for (int t = threadIdx.x; t < N; t += blockDim.x) tw[t] = tw_all[rp.tw_off + t];
-    for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
+    for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = tw_all[rp.tw_off + t];
+    if (rp.mode)
+        for (int t = threadIdx.x; t < N; t += blockDim.x) ch[t] = chirp_all[rp.chirp_off + t];
+    for (int idx = threadIdx.x; idx < G * W; idx += blockDim.x) {
         C v;
         v.x = 0;
         v.y = 0;
@@ -312,7 +377,7 @@ __global__ void __launch_bounds__(256) k_fft_inv(const RowPair *__restrict__ rps
         Rr axx = m < T ? fb[rA] : (Rr)0, ayy = m < T ? fb[rA + 1] : (Rr)0;
         Rr nx = sx + axx, ny = sy + ayy;   // north F_m
         Rr qx = sx - axx, qy = sy - ayy;   // south F_m
-        C *xf = x + (size_t)f * N;
+        C *xf = x + (size_t)f * W;
         if (m == 0) {
             C v;
             v.x = nx;
@@ -329,29 +394,34 @@ __global__ void __launch_bounds__(256) k_fft_inv(const RowPair *__restrict__ rps
         }
     }
     __syncthreads();
-    C *z = fft_passes<C>(x, y, tw, rp, G);
+    C *z = fft_forward<C>(x, y, tw, ch, kern_all + rp.kern_off, rp, G, W);
     for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
         int f = idx / N, k = idx - f * N;
         int fld = f0 + f;
         if (fld >= nfields) continue;
-        C v = z[idx];
+        C v = z[(size_t)f * W + k];
         Rr *g = grid + (long long)fld * npts;
         g[rp.off_n + k] = v.x;
         g[rp.off_s + k] = -v.y;
     }
 }
 
-// Fields per CTA so that the roots plus two work buffers fit in shared memory.
+// Fields per CTA so that roots, chirp and two work buffers of every row fit
+// in shared memory.
 static int fft_fields_per_cta(const st_plan *p, int nfields, size_t *smem)
 {
-    size_t cs = p->prec == P_FP64 ? 16 : 8;
-    size_t per = (size_t)p->max_row * cs;
+    const size_t cs = p->prec == P_FP64 ? 16 : 8;
+    size_t fixed = 0, per = 0;
+    for (const auto &r : p->rowpairs_h) {
+        fixed = std::max(fixed, (size_t)(r.fftlen + (r.mode ? r.N : 0)) * cs);
+        per = std::max(per, (size_t)r.fftlen * cs);
+    }
     const size_t budget = 110 * 1024;
-    int G = (int)((budget / per - 1) / 2);
+    int G = budget > fixed ? (int)((budget - fixed) / (2 * per)) : 1;
     if (G < 1) G = 1;
     if (G > 8) G = 8;
     if (G > nfields) G = nfields;
-    *smem = per * (1 + 2 * (size_t)G);
+    *smem = fixed + 2 * per * (size_t)G;
     return G;
 }
 
@@ -376,28 +446,32 @@ st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t
     case P_FP64: {
         auto k = k_fft_dir<double, S_F64>;
         if ((r = set_smem(k, smem))) return r;
-        k<<<g, 256, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double *)grid, p->npts, nfields, G,
+        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double2 *)p->chirp,
+                                       (const double2 *)p->kern, (const double *)grid, p->npts, nfields, G,
                                p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     case P_FP32: {
         auto k = k_fft_dir<float, S_F32>;
         if ((r = set_smem(k, smem))) return r;
-        k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)grid, p->npts, nfields, G,
+        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
+                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G,
                                p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     case P_TF32X3: {
         auto k = k_fft_dir<float, S_TF32_SPLIT>;
         if ((r = set_smem(k, smem))) return r;
-        k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)grid, p->npts, nfields, G,
+        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
+                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G,
                                p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     default: {
         auto k = k_fft_dir<float, S_BF16_SPLIT>;
         if ((r = set_smem(k, smem))) return r;
-        k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)grid, p->npts, nfields, G,
+        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
+                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G,
                                p->fbop, Cp, Rp, ps, p->T, p->Jp);
         break;
     }
@@ -417,12 +491,14 @@ st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s)
     if (p->prec == P_FP64) {
         auto k = k_fft_inv<double>;
         if ((r = set_smem(k, smem))) return r;
-        k<<<g, 256, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double *)p->fb, Cp, (double *)grid,
+        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double2 *)p->chirp,
+                                       (const double2 *)p->kern, (const double *)p->fb, Cp, (double *)grid,
                                p->npts, nfields, G, p->T, p->Jp);
     } else {
         auto k = k_fft_inv<float>;
         if ((r = set_smem(k, smem))) return r;
-        k<<<g, 256, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float *)p->fb, Cp, (float *)grid,
+        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
+                                       (const float2 *)p->kern, (const float *)p->fb, Cp, (float *)grid,
                                p->npts, nfields, G, p->T, p->Jp);
     }
     ST_CUDA(cudaGetLastError());

@@ -48,12 +48,20 @@ constexpr int MAX_RADICES = 24;
 
 // One northern Gaussian row j (0 = nearest the pole) and its mirror row
 // nlat-1-j; both have N points.
+//  mode 0: the N-point DFT runs as Stockham passes over the radices of N.
+//  mode 1: Bluestein: the N-point DFT is a chirp-weighted circular
+//          convolution of length fftlen = L >= 2N - 1 (L 5-smooth), done with
+//          two L-point Stockham FFTs and a precomputed kernel spectrum.
 struct RowPair {
     int N;                    // points per row
     int M;                    // wavenumbers kept: 0..M
-    int nrad;                 // number of Stockham passes
+    int mode;                 // 0 direct mixed radix, 1 Bluestein
+    int fftlen;               // length of the FFTs run: N (mode 0) or L (mode 1)
+    int nrad;                 // number of Stockham passes of length fftlen
     int rad[MAX_RADICES];     // radix of each pass
-    long long tw_off;         // first of the row's N roots of unity e^{-2 pi i t / N}
+    long long tw_off;         // first of the row's fftlen roots of unity e^{-2 pi i t / fftlen}
+    long long chirp_off;      // mode 1: N chirp values w_k = e^{-i pi k^2 / N}
+    long long kern_off;       // mode 1: L values FFT_L(b) / L, b the conjugate chirp wrapped circularly
     long long off_n;          // offset of the northern row inside one field's grid
     long long off_s;          // offset of the southern row
 };
@@ -105,7 +113,12 @@ struct st_plan {
     std::vector<st::RowPair> rowpairs_h;
     void *tw = nullptr;                  // device roots of unity (double2 or float2)
     long long ntw = 0;
-    int max_row = 0;
+    void *chirp = nullptr;               // Bluestein chirps (double2 or float2)
+    void *kern = nullptr;                // Bluestein kernel spectra (double2 or float2)
+    long long nchirp = 0, nkern = 0;
+    int max_row = 0;                     // largest N
+    int max_fft = 0;                     // largest fftlen
+    int max_chirp = 0;                   // largest N among Bluestein rows
 
     // Legendre data, [0] inverse, [1] direct
     void *tab[2] = {nullptr, nullptr};
@@ -173,6 +186,7 @@ const char *kernel_name(const st_plan *p, int kind);
 // ---- launchers implemented in the .cu files ----
 st_status launch_tables(st_plan *p, cudaStream_t s);
 st_status launch_twiddles(st_plan *p, cudaStream_t s);
+st_status launch_bluestein_setup(st_plan *p, cudaStream_t s);
 st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s);
 st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s);
 st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s);

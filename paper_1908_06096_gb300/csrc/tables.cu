@@ -222,19 +222,132 @@ __global__ void k_twiddles(const RowPair *rp, int J, C *tw)
     int j = blockIdx.y;
     if (j >= J) return;
     RowPair r = rp[j];
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r.N; t += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < r.fftlen; t += gridDim.x * blockDim.x) {
         double sn, cs;
-        sincospi(2.0 * (double)t / (double)r.N, &sn, &cs);
+        sincospi(2.0 * (double)t / (double)r.fftlen, &sn, &cs);
         C v;
-        v.x = cs;
-        v.y = -sn;
+        v.x = (decltype(v.x))cs;
+        v.y = (decltype(v.y))-sn;
         tw[r.tw_off + t] = v;
     }
 }
 
+// ---------------------------------------------------------------- Bluestein set-up
+//
+// Bluestein's identity m k = (m^2 + k^2 - (m - k)^2) / 2 turns the N-point DFT
+//   Z_m = sum_k z_k e^{-2 pi i m k / N}
+// into Z_m = w_m sum_k (z_k w_k) conj(w_{m-k}) with the chirp
+// w_k = e^{-i pi k^2 / N}: a convolution, done circularly at any length
+// L >= 2N - 1 with the conjugate chirp b wrapped around (b_i = conj(w_i) for
+// 0 <= i < N, b_{L-d} = conj(w_d) for 1 <= d < N, zero between).  The plan
+// keeps w and FFT_L(b) / L; both are computed here in FP64 (k^2 reduced
+// mod 2N exactly in integers before the angle is formed).
+
+__device__ inline void chirp_val(long long k, int N, double &c, double &s)
+{
+    long long t = (k * k) % (2LL * N);
+    double sn, cs;
+    sincospi((double)t / (double)N, &sn, &cs);
+    c = cs;
+    s = -sn;  // e^{-i pi t / N}
+}
+
+template <typename C>
+__global__ void k_chirp(const RowPair *rps, int J, C *chirp)
+{
+    int j = blockIdx.y;
+    if (j >= J) return;
+    RowPair r = rps[j];
+    if (r.mode != 1) return;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < r.N; k += gridDim.x * blockDim.x) {
+        double c, s;
+        chirp_val(k, r.N, c, s);
+        C v;
+        v.x = (decltype(v.x))c;
+        v.y = (decltype(v.y))s;
+        chirp[r.chirp_off + k] = v;
+    }
+}
+
+// One CTA per Bluestein row: b in FP64, Stockham passes (one output per
+// thread, roots by sincospi) in a global scratch buffer, result / L.
+template <typename C>
+__global__ void k_bluestein_kern(const RowPair *rps, int J, double2 *scratch, long long nkern, C *kern)
+{
+    int j = blockIdx.x;
+    if (j >= J) return;
+    const RowPair r = rps[j];
+    if (r.mode != 1) return;
+    const int N = r.N, L = r.fftlen;
+    double2 *x = scratch + r.kern_off, *y = scratch + nkern + r.kern_off;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        double2 v = make_double2(0.0, 0.0);
+        long long d = -1;
+        if (i < N) d = i;
+        else if (i > L - N) d = L - i;
+        if (d >= 0) {
+            double c, s;
+            chirp_val(d, N, c, s);
+            v = make_double2(c, -s);  // conj(w_d)
+        }
+        x[i] = v;
+    }
+    __syncthreads();
+    int Lc = 1;
+    for (int q = 0; q < r.nrad; ++q) {
+        const int R = r.rad[q], nb = L / R, step = L / (Lc * R);
+        for (int o = threadIdx.x; o < L; o += blockDim.x) {
+            int k = o % Lc, s_ = (o / Lc) % R, grp = o / (Lc * R);
+            int b = grp * Lc + k;
+            long long e = (long long)(k + s_ * Lc) * step;
+            double ax = 0, ay = 0;
+            for (int rr = 0; rr < R; ++rr) {
+                double2 v = x[b + rr * nb];
+                long long t = (e * rr) % L;
+                double sn, cs;
+                sincospi(2.0 * (double)t / (double)L, &sn, &cs);
+                // v * e^{-2 pi i t / L}
+                ax += v.x * cs + v.y * sn;
+                ay += v.y * cs - v.x * sn;
+            }
+            y[o] = make_double2(ax, ay);
+        }
+        __syncthreads();
+        double2 *t = x;
+        x = y;
+        y = t;
+        Lc *= R;
+    }
+    const double inv = 1.0 / (double)L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        C v;
+        v.x = (decltype(v.x))(x[i].x * inv);
+        v.y = (decltype(v.y))(x[i].y * inv);
+        kern[r.kern_off + i] = v;
+    }
+}
+
+st_status launch_bluestein_setup(st_plan *p, cudaStream_t s)
+{
+    double2 *scratch = nullptr;
+    ST_CUDA(cudaMallocAsync(&scratch, sizeof(double2) * 2 * (size_t)p->nkern, s));
+    dim3 g1((p->max_chirp + 255) / 256, p->J);
+    if (p->prec == P_FP64) {
+        k_chirp<double2><<<g1, 256, 0, s>>>(p->rowpairs, p->J, (double2 *)p->chirp);
+        k_bluestein_kern<double2><<<p->J, 256, 0, s>>>(p->rowpairs, p->J, scratch, p->nkern, (double2 *)p->kern);
+    } else {
+        k_chirp<float2><<<g1, 256, 0, s>>>(p->rowpairs, p->J, (float2 *)p->chirp);
+        k_bluestein_kern<float2><<<p->J, 256, 0, s>>>(p->rowpairs, p->J, scratch, p->nkern, (float2 *)p->kern);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bluestein set-up");
+    return ST_OK;
+}
+
 st_status launch_twiddles(st_plan *p, cudaStream_t s)
 {
-    dim3 grid((p->max_row + 255) / 256, p->J);
+    dim3 grid((p->max_fft + 255) / 256, p->J);
     if (p->prec == P_FP64)
         k_twiddles<double2><<<grid, 256, 0, s>>>(p->rowpairs, p->J, (double2 *)p->tw);
     else
