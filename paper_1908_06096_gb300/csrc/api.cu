@@ -55,18 +55,87 @@ static int smooth_at_least(int n)
     }
 }
 
-// Rough per-field work models (complex multiply-adds) used to pick a row's
-// FFT form: a Stockham pass of radix r costs about N r, a pass over a prime
-// above 5 (one output per thread, table look-ups) about twice that.
-static double direct_cost(int N, const int *rad, int n)
+// Order radices so that consecutive pairs (fused into one pass) match a
+// large radix with a small one: descending, then largest/smallest alternating.
+static void pair_radices(int *rad, int n)
 {
-    double c = 0;
-    for (int q = 0; q < n; ++q) c += (double)N * rad[q] * (rad[q] > 5 ? 2.0 : 1.0);
-    return c;
+    std::vector<int> v(rad, rad + n);
+    std::sort(v.begin(), v.end(), [](int a, int b) { return a > b; });
+    int lo = 0, hi = n - 1, k = 0;
+    while (lo <= hi) {
+        rad[k++] = v[lo++];
+        if (lo <= hi) rad[k++] = v[hi--];
+    }
 }
-static double bluestein_cost(int L, const int *rad, int n)
+
+// Stages fused into one pass when the pair has at most this many points
+// (must match the FFT kernels).
+constexpr int FFT_MAX_FUSED = 16;
+
+// Shared-memory wavefronts of the row's in-place passes under address map
+// `mode`, relative to the conflict-free count (8-byte accesses: two phases of
+// 16 threads; a phase costs its largest number of distinct addresses that
+// share a 8-byte bank slot).  Used to pick the map per row.
+static double fft_conflicts(int L, const int *rad, int n, int mode)
 {
-    return 2.0 * direct_cost(L, rad, n) + 4.0 * L;
+    struct Pass { int Ns, Ra, Rb; };
+    std::vector<Pass> ps;
+    int Ns = L;
+    for (int q = 0; q < n;) {
+        if (q + 1 < n && rad[q] * rad[q + 1] <= FFT_MAX_FUSED) {
+            ps.push_back({Ns, rad[q], rad[q + 1]});
+            Ns /= rad[q] * rad[q + 1];
+            q += 2;
+        } else {
+            ps.push_back({Ns, rad[q], 1});
+            Ns /= rad[q];
+            q += 1;
+        }
+    }
+    double tot = 0, ideal = 0;
+    for (const Pass &P : ps) {
+        const int ma = P.Ns / P.Ra, mb = P.Rb > 1 ? ma / P.Rb : ma, per = L / (P.Ra * P.Rb);
+        for (int w0 = 0; w0 < per; w0 += 32) {
+            const int nt = std::min(32, per - w0);
+            for (int ra = 0; ra < P.Ra; ++ra)
+                for (int rb = 0; rb < P.Rb; ++rb)
+                    for (int h = 0; h < nt; h += 16) {
+                        int addr[16], cnt[16] = {0};
+                        int m = 0;
+                        for (int t = w0 + h; t < w0 + std::min(nt, h + 16); ++t) {
+                            const int b = t / mb, n1 = t % mb;
+                            const int i = b * P.Ns + n1 + ra * ma + (P.Rb > 1 ? rb * mb : 0);
+                            const int a = fft_swz(i, mode);
+                            bool seen = false;
+                            for (int u = 0; u < m; ++u) seen |= addr[u] == a;
+                            if (!seen) addr[m++] = a;
+                        }
+                        int worst = 0;
+                        for (int u = 0; u < m; ++u) worst = std::max(worst, ++cnt[addr[u] & 15]);
+                        tot += worst;
+                        ideal += 1;
+                    }
+        }
+    }
+    return ideal > 0 ? tot / ideal : 1.0;
+}
+
+static int pick_swizzle(int L, const int *rad, int n)
+{
+    int best = 0;
+    double bc = fft_conflicts(L, rad, n, 0);
+    for (int mode = 1; mode <= 3; ++mode) {
+        double c = fft_conflicts(L, rad, n, mode);
+        if (c < bc - 1e-9) { bc = c; best = mode; }
+    }
+    return best;
+}
+
+static bool smooth5(const int *rad, int n)
+{
+    for (int q = 0; q < n; ++q)
+        if (rad[q] > 5) return false;
+    return true;
 }
 
 template <typename T>
@@ -229,14 +298,13 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     if ((r = dmalloc(p, &p->w, sizeof(double) * nlat))) return r;
     if ((r = launch_gauss(nlat, p->mu, p->w, s))) return r;
 
-    // FFT rows: mixed radix over N, or Bluestein over a 5-smooth L >= 2N - 1
-    // where N has a large prime factor and that is cheaper (FP64 plans keep
-    // the direct form: their parity, not their speed, is what they are for)
+    // FFT rows: mixed radix over N where N is 5-smooth, otherwise Bluestein
+    // over a 5-smooth L >= 2N - 1
     p->rowpairs_h.resize(J);
     long long off = 0, tw = 0, nch = 0, nkn = 0;
     std::vector<long long> roff(nlat);
     for (int j = 0; j < nlat; ++j) { roff[j] = off; off += p->rows[j]; }
-    p->max_row = p->max_fft = p->max_chirp = 0;
+    p->max_row = p->max_fft = p->max_chirp = p->max_fft_smem = 0;
     for (int j = 0; j < J; ++j) {
         RowPair &rp = p->rowpairs_h[j];
         memset(&rp, 0, sizeof(rp));
@@ -250,7 +318,9 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
         const int L = smooth_at_least(2 * rp.N - 1);
         int radL[MAX_RADICES];
         int nL = factorize(L, radL);
-        if (p->prec != P_FP64 && bluestein_cost(L, radL, nL) < direct_cost(rp.N, radN, nN)) {
+        pair_radices(radN, nN);
+        pair_radices(radL, nL);
+        if (!smooth5(radN, nN)) {
             rp.mode = 1;
             rp.fftlen = L;
             rp.nrad = nL;
@@ -266,6 +336,8 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
             rp.nrad = nN;
             memcpy(rp.rad, radN, sizeof(int) * nN);
         }
+        rp.swz = pick_swizzle(rp.fftlen, rp.rad, rp.nrad);
+        p->max_fft_smem = std::max(p->max_fft_smem, fft_swz_size(rp.fftlen, rp.swz));
         rp.tw_off = tw;
         tw += rp.fftlen;
         rp.off_n = roff[j];

@@ -6,10 +6,21 @@
 // One CTA takes one northern row j and its mirror row (same length N) for a
 // group of G fields.  The two real rows of a field are packed as one complex
 // sequence z = north + i south, so a single complex FFT of length N serves
-// both.  The transform runs as Stockham autosort passes in shared memory, one
-// pass per prime-power factor: radix 2, 3, 4 and 5 butterflies are written
-// out; any other prime factor is evaluated as a direct DFT over that factor
-// (one output per thread).
+// both.  Every transform runs in place in shared memory (one buffer per
+// field) as mixed-radix passes over radices 2, 3, 4, 5; each pass fuses two
+// radix stages in registers (a 16-point pass for 4 x 4), so a 5184-point FFT
+// takes 4 trips through shared memory.  Roots of unity, chirps and kernel
+// spectra are read through the read-only cache.
+//
+//  mode 0 (N 5-smooth): decimation-in-frequency passes; the output sits in
+//          digit-reversed order and is read through the index map pos(m).
+//  mode 1 (Bluestein): the N-point DFT as a chirp-weighted circular
+//          convolution of length L >= 2N - 1:
+//              Z_m = w_m sum_k (z_k w_k) conj(w_{m-k}),  w_k = e^{-i pi k^2 / N}
+//          done as DIF (natural -> digit-reversed), a pointwise product with
+//          the kernel spectrum stored in that same digit-reversed order, and
+//          DIT (digit-reversed -> natural), with IFFT(v) = conj(FFT(conj v))/L
+//          (the 1/L is folded into the stored kernel).
 //
 // Direct stage: grid rows -> E = F(north) + F(south), O = F(north) - F(south)
 // for m <= M_j, scaled by 1/N, written in the storage the direct Legendre
@@ -21,7 +32,7 @@
 
 namespace st {
 
-constexpr int FFT_THREADS = 512;
+constexpr int FFT_THREADS = 256;
 
 template <typename R> struct CT;
 template <> struct CT<double> { typedef double2 T; };
@@ -36,21 +47,15 @@ template <typename C> __device__ inline C cmul(C a, C b)
     r.y = a.x * b.y + a.y * b.x;
     return r;
 }
+template <typename C> __device__ inline C cconj(C a) { a.y = -a.y; return a; }
 // multiply by -i
 template <typename C> __device__ inline C cmul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
 
-// Radix-R butterfly on v[0..R-1] with W = e^{-2 pi i / R}.
-template <int R, typename C> __device__ inline void dft_small(C *v);
+// ------------------------------------------------------------------ R-point DFTs, W = e^{-2 pi i / R}
 
-template <> __device__ inline void dft_small<2, double2>(double2 *v)
+template <typename C> __device__ inline void dft2(C *v)
 {
-    double2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
-}
-template <> __device__ inline void dft_small<2, float2>(float2 *v)
-{
-    float2 a = v[0], b = v[1];
+    C a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
 }
@@ -65,7 +70,7 @@ template <typename C> __device__ inline void dft4(C *v)
     v[3] = csub(b, d);
 }
 
-// W = c + i s with c = -1/2, s = -sqrt(3)/2
+// W = c + i s, c = -1/2, s = -sqrt(3)/2
 template <typename C> __device__ inline void dft3(C *v)
 {
     typedef decltype(v[0].x) Rr;
@@ -110,134 +115,252 @@ template <typename C> __device__ inline void dft5(C *v)
     v[3] = csub(a2, b2);
 }
 
-// One Stockham pass of radix R (2, 3, 4 or 5) over G sequences of length N in
-// shared memory: src -> dst, L = product of the radices of earlier passes.
-template <int R, typename C>
-__device__ inline void pass_small(const C *src, C *dst, const C *tw, int N, int S, int L, int G)
+template <int R, typename C> __device__ inline void dftR(C *v)
 {
-    int nb = N / R;
-    int step = N / (L * R);
-    for (int idx = threadIdx.x; idx < G * nb; idx += blockDim.x) {
-        int f = idx / nb, b = idx - f * nb;
-        int k = b % L, grp = b / L;
-        const C *s = src + (size_t)f * S;
+    if (R == 2) dft2(v);
+    if (R == 3) dft3(v);
+    if (R == 4) dft4(v);
+    if (R == 5) dft5(v);
+}
+
+// ------------------------------------------------------------------ in-place passes
+//
+// DIF stage of radix R on blocks of size Ns: for each block and n1 < Ns/R,
+// the R elements n1 + r Ns/R go through an R-point DFT, output q is then
+// multiplied by W_Ns^{n1 q}, and written back to the same R places.  The DIT
+// stage is its transpose (twiddle first, then the DFT) and runs the stages in
+// the opposite order.  A pass fuses two consecutive stages (Ra on blocks of
+// Ns, then Rb on the sub-blocks of Ns/Ra) in registers.  tw holds
+// e^{-2 pi i t / L}; W_Ns^t = tw[t L / Ns].  Each stage loads one base root
+// and forms its powers by multiplication.  Element i of a field lives at
+// shared-memory slot Swz(i).
+
+struct Swz {
+    int a, pm, xm;
+    __device__ explicit Swz(int mode)
+        : a(mode == 2 ? 5 : 4), pm((mode == 1 || mode == 2) ? -1 : 0), xm(mode == 3 ? 15 : 0) {}
+    __device__ int operator()(int i) const { return (i + ((i >> a) & pm)) ^ ((i >> 4) & xm); }
+};
+
+// n / d for 0 <= n < 2^22 without an integer divide: float reciprocal, then
+// one correction step.
+struct FastDiv {
+    int d;
+    float inv;
+    __device__ explicit FastDiv(int d_) : d(d_), inv(1.0f / (float)d_) {}
+    __device__ int operator()(int n) const
+    {
+        int q = __float2int_rz((float)n * inv);
+        const int r = n - q * d;
+        if (r >= d) ++q;
+        else if (r < 0) --q;
+        return q;
+    }
+};
+
+// v[q] *= w^q, q = 1 .. R-1
+template <int R, typename C> __device__ inline void twiddle_powers(C *v, C w)
+{
+    C p = w;
+#pragma unroll
+    for (int q = 1; q < R; ++q) {
+        v[q] = cmul(v[q], p);
+        if (q + 1 < R) p = cmul(p, w);
+    }
+}
+
+template <int Ra, int Rb, bool DIT, typename C>
+__device__ inline void pass2(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, Swz sw,
+                             const C *__restrict__ kern)
+{
+    const int ma = Ns / Ra, mb = ma / Rb;
+    const int per = L / (Ra * Rb);
+    const int sa = L / Ns, sb = L / ma;
+    const C c = __ldg(&tw[mb * sa]);  // e^{-2 pi i / (Ra Rb)}
+    const FastDiv dper(per), dmb(mb);
+    for (int idx = threadIdx.x; idx < G * per; idx += blockDim.x) {
+        const int f = dper(idx), t = idx - f * per;
+        const int b = dmb(t), n1 = t - b * mb;
+        C *xf = x + (size_t)f * S;
+        const int i0 = b * Ns + n1;
+        C v[Ra][Rb];
+#pragma unroll
+        for (int ra = 0; ra < Ra; ++ra)
+#pragma unroll
+            for (int rb = 0; rb < Rb; ++rb) v[ra][rb] = xf[sw(i0 + ra * ma + rb * mb)];
+        const C wa0 = __ldg(&tw[n1 * sa]);
+        const C wb = __ldg(&tw[n1 * sb]);
+        if (!DIT) {
+            C wa = wa0;
+#pragma unroll
+            for (int rb = 0; rb < Rb; ++rb) {
+                C u[Ra];
+#pragma unroll
+                for (int ra = 0; ra < Ra; ++ra) u[ra] = v[ra][rb];
+                dftR<Ra>(u);
+                twiddle_powers<Ra>(u, wa);
+#pragma unroll
+                for (int q = 0; q < Ra; ++q) v[q][rb] = u[q];
+                if (rb + 1 < Rb) wa = cmul(wa, c);
+            }
+#pragma unroll
+            for (int ra = 0; ra < Ra; ++ra) {
+                dftR<Rb>(v[ra]);
+                twiddle_powers<Rb>(v[ra], wb);
+            }
+        } else {
+#pragma unroll
+            for (int ra = 0; ra < Ra; ++ra) {
+                twiddle_powers<Rb>(v[ra], wb);
+                dftR<Rb>(v[ra]);
+            }
+            C wa = wa0;
+#pragma unroll
+            for (int rb = 0; rb < Rb; ++rb) {
+                C u[Ra];
+#pragma unroll
+                for (int r = 0; r < Ra; ++r) u[r] = v[r][rb];
+                twiddle_powers<Ra>(u, wa);
+                dftR<Ra>(u);
+#pragma unroll
+                for (int q = 0; q < Ra; ++q) v[q][rb] = u[q];
+                if (rb + 1 < Rb) wa = cmul(wa, c);
+            }
+        }
+        if (kern) {
+            // last DIF pass of a Bluestein row: times the kernel spectrum (kept in
+            // this digit-reversed order), then conjugated for the second FFT
+#pragma unroll
+            for (int ra = 0; ra < Ra; ++ra)
+#pragma unroll
+                for (int rb = 0; rb < Rb; ++rb)
+                    v[ra][rb] = cconj(cmul(v[ra][rb], __ldg(&kern[i0 + ra * ma + rb * mb])));
+        }
+#pragma unroll
+        for (int ra = 0; ra < Ra; ++ra)
+#pragma unroll
+            for (int rb = 0; rb < Rb; ++rb) xf[sw(i0 + ra * ma + rb * mb)] = v[ra][rb];
+    }
+}
+
+template <int R, bool DIT, typename C>
+__device__ inline void pass1(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, Swz sw,
+                             const C *__restrict__ kern)
+{
+    const int m = Ns / R;
+    const int per = L / R;
+    const int sa = L / Ns;
+    const FastDiv dper(per), dm(m);
+    for (int idx = threadIdx.x; idx < G * per; idx += blockDim.x) {
+        const int f = dper(idx), t = idx - f * per;
+        const int b = dm(t), n1 = t - b * m;
+        C *xf = x + (size_t)f * S;
+        const int i0 = b * Ns + n1;
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[b + r * nb];
-        if (k) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * k * step]);
+        for (int r = 0; r < R; ++r) v[r] = xf[sw(i0 + r * m)];
+        const C w = __ldg(&tw[n1 * sa]);
+        if (!DIT) {
+            dftR<R>(v);
+            twiddle_powers<R>(v, w);
+        } else {
+            twiddle_powers<R>(v, w);
+            dftR<R>(v);
         }
-        if (R == 2) dft_small<2, C>(v);
-        if (R == 3) dft3(v);
-        if (R == 4) dft4(v);
-        if (R == 5) dft5(v);
-        C *d = dst + (size_t)f * S + (size_t)grp * L * R + k;
+        if (kern) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) d[r * L] = v[r];
+            for (int r = 0; r < R; ++r) v[r] = cconj(cmul(v[r], __ldg(&kern[i0 + r * m])));
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) xf[sw(i0 + r * m)] = v[r];
     }
 }
 
-// Stockham pass of any radix R as a direct DFT over the factor, one output
-// per thread: out[grp L R + s L + k] = sum_r src[b + r N/R] W_N^{r (k + s L) N/(L R)}.
-template <typename C>
-__device__ inline void pass_generic(const C *src, C *dst, const C *tw, int N, int S, int L, int R, int G)
+template <bool DIT, typename C>
+__device__ inline void run_pass2(int Ra, int Rb, C *x, const C *tw, int L, int S, int Ns, int G, Swz sw,
+                                 const C *kern)
 {
-    int nb = N / R;
-    int step = N / (L * R);
-    for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
-        int f = idx / N, o = idx - f * N;
-        int k = o % L;
-        int s_ = (o / L) % R;
-        int grp = o / (L * R);
-        int b = grp * L + k;
-        const C *s = src + (size_t)f * S;
-        int e = (k + s_ * L) * step;  // < N
-        int ex = 0;
-        C acc;
-        acc.x = 0;
-        acc.y = 0;
-        for (int r = 0; r < R; ++r) {
-            C x = s[b + r * nb];
-            C t = tw[ex];
-            acc.x += x.x * t.x - x.y * t.y;
-            acc.y += x.x * t.y + x.y * t.x;
-            ex += e;
-            if (ex >= N) ex -= N;
-        }
-        dst[(size_t)f * S + o] = acc;
-    }
+#define ST_P2(A, B) \
+    if (Ra == A && Rb == B) { pass2<A, B, DIT, C>(x, tw, L, S, Ns, G, sw, kern); return; }
+    ST_P2(4, 4) ST_P2(4, 3) ST_P2(3, 4) ST_P2(3, 3) ST_P2(4, 2) ST_P2(2, 4) ST_P2(3, 5) ST_P2(5, 3)
+    ST_P2(2, 5) ST_P2(5, 2) ST_P2(2, 3) ST_P2(3, 2) ST_P2(2, 2)
+#undef ST_P2
 }
 
-// Runs all passes of length n = rp.fftlen over G sequences spaced S apart;
-// returns the buffer that holds the result.
-template <typename C>
-__device__ C *fft_passes(C *x, C *y, const C *tw, const RowPair &rp, int G, int S)
+template <bool DIT, typename C>
+__device__ inline void run_pass1(int R, C *x, const C *tw, int L, int S, int Ns, int G, Swz sw, const C *kern)
 {
-    int L = 1;
-    const int n = rp.fftlen;
-    for (int q = 0; q < rp.nrad; ++q) {
-        int R = rp.rad[q];
-        switch (R) {
-        case 2: pass_small<2, C>(x, y, tw, n, S, L, G); break;
-        case 3: pass_small<3, C>(x, y, tw, n, S, L, G); break;
-        case 4: pass_small<4, C>(x, y, tw, n, S, L, G); break;
-        case 5: pass_small<5, C>(x, y, tw, n, S, L, G); break;
-        default: pass_generic<C>(x, y, tw, n, S, L, R, G); break;
+    if (R == 2) pass1<2, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
+    else if (R == 3) pass1<3, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
+    else if (R == 4) pass1<4, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
+    else pass1<5, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
+}
+
+// Stages are fused in pairs when the pair holds at most 16 points (the
+// register budget); fusing or not does not change the result.
+constexpr int MAX_FUSED = 16;
+
+// All DIF stages over rp.rad (natural -> digit-reversed).  With `kern`, the
+// last pass also multiplies by the kernel spectrum and conjugates.
+template <typename C>
+__device__ void fft_dif(C *x, const C *tw, const RowPair &rp, int G, int S, const C *kern)
+{
+    const int L = rp.fftlen;
+    const Swz sw(rp.swz);
+    int Ns = L;
+    for (int q = 0; q < rp.nrad;) {
+        if (q + 1 < rp.nrad && rp.rad[q] * rp.rad[q + 1] <= MAX_FUSED) {
+            const bool last = q + 2 >= rp.nrad;
+            run_pass2<false, C>(rp.rad[q], rp.rad[q + 1], x, tw, L, S, Ns, G, sw, last ? kern : nullptr);
+            Ns /= rp.rad[q] * rp.rad[q + 1];
+            q += 2;
+        } else {
+            const bool last = q + 1 >= rp.nrad;
+            run_pass1<false, C>(rp.rad[q], x, tw, L, S, Ns, G, sw, last ? kern : nullptr);
+            Ns /= rp.rad[q];
+            q += 1;
         }
         __syncthreads();
-        C *t = x;
-        x = y;
-        y = t;
-        L *= R;
     }
-    return x;
 }
 
-// Forward N-point DFT of the G sequences in x (each in the first N slots of
-// a stride-S slot); returns the buffer holding Z_0 .. Z_{N-1} per field.
-// Mode 1 (Bluestein): Z_m = w_m conj(FFT_L(conj(FFT_L(z w) * kern)))_m with
-// kern = FFT_L(b) / L, which is the circular convolution with b written
-// through the conjugation identity IFFT(v) = conj(FFT(conj(v))) / L.
+// All DIT stages (digit-reversed -> natural): the stages in reverse order.
 template <typename C>
-__device__ C *fft_forward(C *x, C *y, const C *tw, const C *chirp, const C *__restrict__ kern, const RowPair &rp,
-                          int G, int S)
+__device__ void fft_dit(C *x, const C *tw, const RowPair &rp, int G, int S)
 {
-    if (rp.mode == 0) return fft_passes<C>(x, y, tw, rp, G, S);
-    const int N = rp.N, L = rp.fftlen;
-    for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
-        int f = idx / L, k = idx - f * L;
-        C *v = x + (size_t)f * S + k;
-        if (k < N) {
-            *v = cmul(*v, chirp[k]);
+    const int L = rp.fftlen;
+    const Swz sw(rp.swz);
+    int Ns = 1;
+    for (int q = rp.nrad - 1; q >= 0;) {
+        if (q >= 1 && rp.rad[q - 1] * rp.rad[q] <= MAX_FUSED) {
+            Ns *= rp.rad[q - 1] * rp.rad[q];
+            run_pass2<true, C>(rp.rad[q - 1], rp.rad[q], x, tw, L, S, Ns, G, sw, (const C *)nullptr);
+            q -= 2;
         } else {
-            C z;
-            z.x = 0;
-            z.y = 0;
-            *v = z;
+            Ns *= rp.rad[q];
+            run_pass1<true, C>(rp.rad[q], x, tw, L, S, Ns, G, sw, (const C *)nullptr);
+            q -= 1;
         }
+        __syncthreads();
     }
-    __syncthreads();
-    C *a = fft_passes<C>(x, y, tw, rp, G, S);
-    C *other = a == x ? y : x;
-    for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
-        int f = idx / L, k = idx - f * L;
-        C *v = a + (size_t)f * S + k;
-        C t = cmul(*v, kern[k]);
-        t.y = -t.y;
-        *v = t;
-    }
-    __syncthreads();
-    C *q = fft_passes<C>(a, other, tw, rp, G, S);
-    for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
-        int f = idx / N, m = idx - f * N;
-        C *v = q + (size_t)f * S + m;
-        C t = *v;
-        t.y = -t.y;
-        *v = cmul(chirp[m], t);
-    }
-    __syncthreads();
-    return q;
+}
+
+// Forward N-point DFT of each field's sequence, already in x (mode 0: natural
+// order; mode 1: premultiplied by the chirp and zero up to L).  Afterwards
+// fft_value(m) gives Z_m.
+template <typename C>
+__device__ inline void fft_forward(C *x, const C *tw, const C *__restrict__ kern, const RowPair &rp, int G, int S)
+{
+    fft_dif<C>(x, tw, rp, G, S, rp.mode == 1 ? kern : nullptr);
+    if (rp.mode == 1) fft_dit<C>(x, tw, rp, G, S);
+}
+
+template <typename C>
+__device__ inline C fft_value(const C *xf, const C *__restrict__ chirp, const RowPair &rp, int m)
+{
+    const Swz sw(rp.swz);
+    if (rp.mode == 0) return xf[sw(dif_pos(m, rp))];
+    return cmul(__ldg(&chirp[m]), cconj(xf[sw(m)]));
 }
 
 __device__ inline float round_tf32_f(float x)
@@ -270,55 +393,77 @@ __device__ inline void store_val(void *base, long long idx, long long plane_stri
     }
 }
 
+// Store the (re, im) pair of columns (c, c + 1) of row r; c is even, so
+// row-major storage takes one 8-, 16- or (per plane) 4-byte store.
+template <int S, typename Rr>
+__device__ inline void store_pair(void *base, long long r, int c, int Cp, long long Rp, long long ps, Rr re, Rr im)
+{
+    const long long idx = op_index(S, r, c, Cp, Rp);
+    if (S == S_F64) {
+        *(double2 *)((double *)base + idx) = make_double2((double)re, (double)im);
+    } else if (S == S_F32) {
+        *(float2 *)((float *)base + idx) = make_float2((float)re, (float)im);
+    } else if (S == S_BF16_SPLIT) {
+        const float fr = (float)re, fi = (float)im;
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(fr, fi);
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(fr - __low2float(hi), fi - __high2float(hi));
+        *(__nv_bfloat162 *)((__nv_bfloat16 *)base + idx) = hi;
+        *(__nv_bfloat162 *)((__nv_bfloat16 *)base + idx + ps) = lo;
+    } else {
+        store_val<S, Rr>(base, idx, ps, re);
+        store_val<S, Rr>(base, op_index(S, r, c + 1, Cp, Rp), ps, im);
+    }
+}
+
+template <typename Rr> struct FftBounds { static constexpr int MINB = 3; };
+template <> struct FftBounds<double> { static constexpr int MINB = 1; };
+
 template <typename Rr, int S>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_dir(const RowPair *__restrict__ rps,
-                                                         const typename CT<Rr>::T *__restrict__ tw_all,
-                                                         const typename CT<Rr>::T *__restrict__ chirp_all,
-                                                         const typename CT<Rr>::T *__restrict__ kern_all,
-                                                         const Rr *__restrict__ grid, long long npts, int nfields, int G,
-                                                         void *fb, int Cp, long long Rp, long long plane_stride, int T,
-                                                         int Jp)
+__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
+    k_fft_dir(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
+              const typename CT<Rr>::T *__restrict__ chirp_all, const typename CT<Rr>::T *__restrict__ kern_all,
+              const Rr *__restrict__ grid, long long npts, int nfields, int G, int Sslot, void *fb, int Cp,
+              long long Rp, long long plane_stride, int T, int Jp)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int j = blockIdx.y;
     const RowPair rp = rps[j];
-    const int N = rp.N, W = rp.fftlen;
-    C *tw = (C *)smem_raw;
-    C *ch = tw + W;
-    C *x = ch + (rp.mode ? N : 0);
-    C *y = x + (size_t)G * W;
+    const int N = rp.N, W = rp.fftlen, SL = Sslot;
+    C *x = (C *)smem_raw;
+    const C *tw = tw_all + rp.tw_off;
+    const C *chirp = chirp_all + rp.chirp_off;
     const int f0 = blockIdx.x * G;
+    const Swz sw(rp.swz);
 
-    for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = tw_all[rp.tw_off + t];
-    if (rp.mode)
-        for (int t = threadIdx.x; t < N; t += blockDim.x) ch[t] = chirp_all[rp.chirp_off + t];
-    for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
-        int f = idx / N, k = idx - f * N;
-        int fld = f0 + f;
+    const FastDiv dW(W);
+    for (int idx = threadIdx.x; idx < G * W; idx += blockDim.x) {
+        const int f = dW(idx), k = idx - f * W;
+        const int fld = f0 + f;
         C v;
         v.x = 0;
         v.y = 0;
-        if (fld < nfields) {
+        if (fld < nfields && k < N) {
             const Rr *g = grid + (long long)fld * npts;
             v.x = g[rp.off_n + k];
             v.y = g[rp.off_s + k];
+            if (rp.mode == 1) v = cmul(v, __ldg(&chirp[k]));
         }
-        x[(size_t)f * W + k] = v;
+        x[(size_t)f * SL + sw(k)] = v;
     }
     __syncthreads();
-    C *z = fft_forward<C>(x, y, tw, ch, kern_all + rp.kern_off, rp, G, W);
+    fft_forward<C>(x, tw, kern_all + rp.kern_off, rp, G, SL);
 
     const Rr inv = (Rr)1.0 / (Rr)N;
     const int M = rp.M;
+    const FastDiv dG(G);
     for (int idx = threadIdx.x; idx < (M + 1) * G; idx += blockDim.x) {
-        int m = idx / G, f = idx - m * G;
-        int fld = f0 + f;
+        const int m = dG(idx), f = idx - m * G;
+        const int fld = f0 + f;
         if (fld >= nfields) continue;
-        const C *zf = z + (size_t)f * W;
-        C zm = zf[m];
-        C zc = zf[m == 0 ? 0 : N - m];
-        zc.y = -zc.y;
+        const C *xf = x + (size_t)f * SL;
+        C zm = fft_value<C>(xf, chirp, rp, m);
+        C zc = cconj(m == 0 ? zm : fft_value<C>(xf, chirp, rp, N - m));
         // north spectrum A = (zm + zc)/2, south spectrum B = -i (zm - zc)/2
         Rr ax = (zm.x + zc.x) * (Rr)0.5, ay = (zm.y + zc.y) * (Rr)0.5;
         Rr dx = (zm.x - zc.x) * (Rr)0.5, dy = (zm.y - zc.y) * (Rr)0.5;
@@ -327,101 +472,104 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_dir(const RowPair *__restri
         Rr ox = (ax - bx) * inv, oy = (ay - by) * inv;
         if (m == 0) { ey = 0; oy = 0; }
         const long long rE = (long long)m * Jp + j, rO = ((long long)(T + 1) + m) * Jp + j;
-        store_val<S, Rr>(fb, op_index(S, rE, 2 * fld, Cp, Rp), plane_stride, ex);
-        store_val<S, Rr>(fb, op_index(S, rE, 2 * fld + 1, Cp, Rp), plane_stride, ey);
-        store_val<S, Rr>(fb, op_index(S, rO, 2 * fld, Cp, Rp), plane_stride, ox);
-        store_val<S, Rr>(fb, op_index(S, rO, 2 * fld + 1, Cp, Rp), plane_stride, oy);
+        store_pair<S, Rr>(fb, rE, 2 * fld, Cp, Rp, plane_stride, ex, ey);
+        store_pair<S, Rr>(fb, rO, 2 * fld, Cp, Rp, plane_stride, ox, oy);
     }
 }
 
 template <typename Rr>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_inv(const RowPair *__restrict__ rps,
-                                                         const typename CT<Rr>::T *__restrict__ tw_all,
-                                                         const typename CT<Rr>::T *__restrict__ chirp_all,
-                                                         const typename CT<Rr>::T *__restrict__ kern_all,
-                                                         const Rr *__restrict__ fb, int Cp, Rr *__restrict__ grid,
-                                                         long long npts, int nfields, int G, int T, int Jp)
+__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
+    k_fft_inv(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
+              const typename CT<Rr>::T *__restrict__ chirp_all, const typename CT<Rr>::T *__restrict__ kern_all,
+              const Rr *__restrict__ fb, int Cp, Rr *__restrict__ grid, long long npts, int nfields, int G,
+              int Sslot, int T, int Jp)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int j = blockIdx.y;
     const RowPair rp = rps[j];
-    const int N = rp.N, W = rp.fftlen;
-    C *tw = (C *)smem_raw;
-    C *ch = tw + W;
-    C *x = ch + (rp.mode ? N : 0);
-    C *y = x + (size_t)G * W;
+    const int N = rp.N, S = Sslot;
+    C *x = (C *)smem_raw;
+    const C *tw = tw_all + rp.tw_off;
+    const C *chirp = chirp_all + rp.chirp_off;
     const int f0 = blockIdx.x * G;
+    const Swz sw(rp.swz);
 
-    for (int t = threadIdx.x; t < W; t += blockDim.x) tw[t] = tw_all[rp.tw_off + t];
-    if (rp.mode)
-        for (int t = threadIdx.x; t < N; t += blockDim.x) ch[t] = chirp_all[rp.chirp_off + t];
-    for (int idx = threadIdx.x; idx < G * W; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < G * S; idx += blockDim.x) {
         C v;
         v.x = 0;
         v.y = 0;
         x[idx] = v;
     }
     __syncthreads();
-    // conj(Z): Z[m] = Xn + i Xs, Z[N-m] = conj(Xn) + i conj(Xs), Z[0] = Re Xn + i Re Xs
+    // conj(Z): Z[m] = Xn + i Xs, Z[N-m] = conj(Xn) + i conj(Xs), Z[0] = Re Xn + i Re Xs,
+    // times the chirp at the same place for Bluestein rows
+    typedef typename CT<Rr>::T C2;
     const int M = rp.M;
+    const FastDiv dG(G);
     for (int idx = threadIdx.x; idx < (M + 1) * G; idx += blockDim.x) {
-        int m = idx / G, f = idx - m * G;
-        int fld = f0 + f;
+        const int m = dG(idx), f = idx - m * G;
+        const int fld = f0 + f;
         if (fld >= nfields) continue;
-        long long rS = ((long long)m * Jp + j) * Cp + 2 * fld;
-        long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * fld;
+        const long long rS = ((long long)m * Jp + j) * Cp + 2 * fld;
+        const long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * fld;
         // the odd-parity half of m = T is empty (no n = T + 1), so its rows are
         // never written by the Legendre stage: A = 0 there
-        Rr sx = fb[rS], sy = fb[rS + 1];
-        Rr axx = m < T ? fb[rA] : (Rr)0, ayy = m < T ? fb[rA + 1] : (Rr)0;
-        Rr nx = sx + axx, ny = sy + ayy;   // north F_m
-        Rr qx = sx - axx, qy = sy - ayy;   // south F_m
-        C *xf = x + (size_t)f * W;
+        const C2 sv = *(const C2 *)(fb + rS);
+        C2 av;
+        av.x = 0;
+        av.y = 0;
+        if (m < T) av = *(const C2 *)(fb + rA);
+        const Rr sx = sv.x, sy = sv.y, axx = av.x, ayy = av.y;
+        const Rr nx = sx + axx, ny = sy + ayy;  // north F_m
+        const Rr qx = sx - axx, qy = sy - ayy;  // south F_m
+        C *xf = x + (size_t)f * S;
         if (m == 0) {
             C v;
             v.x = nx;
             v.y = -qx;
-            xf[0] = v;
+            if (rp.mode == 1) v = cmul(v, __ldg(&chirp[0]));
+            xf[sw(0)] = v;
         } else {
             C a, b;
             a.x = nx - qy;
             a.y = -(ny + qx);
             b.x = nx + qy;
             b.y = ny - qx;
-            xf[m] = a;
-            xf[N - m] = b;
+            if (rp.mode == 1) {
+                a = cmul(a, __ldg(&chirp[m]));
+                b = cmul(b, __ldg(&chirp[N - m]));
+            }
+            xf[sw(m)] = a;
+            xf[sw(N - m)] = b;
         }
     }
     __syncthreads();
-    C *z = fft_forward<C>(x, y, tw, ch, kern_all + rp.kern_off, rp, G, W);
+    fft_forward<C>(x, tw, kern_all + rp.kern_off, rp, G, S);
+    const FastDiv dN(N);
     for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
-        int f = idx / N, k = idx - f * N;
-        int fld = f0 + f;
+        const int f = dN(idx), k = idx - f * N;
+        const int fld = f0 + f;
         if (fld >= nfields) continue;
-        C v = z[(size_t)f * W + k];
+        const C v = fft_value<C>(x + (size_t)f * S, chirp, rp, k);
         Rr *g = grid + (long long)fld * npts;
         g[rp.off_n + k] = v.x;
         g[rp.off_s + k] = -v.y;
     }
 }
 
-// Fields per CTA so that roots, chirp and two work buffers of every row fit
-// in shared memory.
+// Fields per CTA: one shared-memory buffer of fftlen complex values each,
+// within a per-CTA budget that leaves room for several CTAs per SM.
 static int fft_fields_per_cta(const st_plan *p, int nfields, size_t *smem)
 {
     const size_t cs = p->prec == P_FP64 ? 16 : 8;
-    size_t fixed = 0, per = 0;
-    for (const auto &r : p->rowpairs_h) {
-        fixed = std::max(fixed, (size_t)(r.fftlen + (r.mode ? r.N : 0)) * cs);
-        per = std::max(per, (size_t)r.fftlen * cs);
-    }
-    const size_t budget = 110 * 1024;
-    int G = budget > fixed ? (int)((budget - fixed) / (2 * per)) : 1;
+    const size_t per = (size_t)p->max_fft_smem * cs;
+    const size_t budget = p->prec == P_FP64 ? 110 * 1024 : 56 * 1024;
+    int G = (int)(budget / per);
     if (G < 1) G = 1;
     if (G > 8) G = 8;
     if (G > nfields) G = nfields;
-    *smem = fixed + 2 * per * (size_t)G;
+    *smem = per * (size_t)G;
     return G;
 }
 
@@ -447,32 +595,32 @@ st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t
         auto k = k_fft_dir<double, S_F64>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double2 *)p->chirp,
-                                       (const double2 *)p->kern, (const double *)grid, p->npts, nfields, G,
-                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
+                                       (const double2 *)p->kern, (const double *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop,
+                                       Cp, Rp, ps, p->T, p->Jp);
         break;
     }
     case P_FP32: {
         auto k = k_fft_dir<float, S_F32>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G,
-                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
+                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop, Cp,
+                                       Rp, ps, p->T, p->Jp);
         break;
     }
     case P_TF32X3: {
         auto k = k_fft_dir<float, S_TF32_SPLIT>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G,
-                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
+                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop, Cp,
+                                       Rp, ps, p->T, p->Jp);
         break;
     }
     default: {
         auto k = k_fft_dir<float, S_BF16_SPLIT>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G,
-                               p->fbop, Cp, Rp, ps, p->T, p->Jp);
+                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop, Cp,
+                                       Rp, ps, p->T, p->Jp);
         break;
     }
     }
@@ -492,14 +640,14 @@ st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s)
         auto k = k_fft_inv<double>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double2 *)p->chirp,
-                                       (const double2 *)p->kern, (const double *)p->fb, Cp, (double *)grid,
-                               p->npts, nfields, G, p->T, p->Jp);
+                                       (const double2 *)p->kern, (const double *)p->fb, Cp, (double *)grid, p->npts,
+                                       nfields, G, p->max_fft_smem, p->T, p->Jp);
     } else {
         auto k = k_fft_inv<float>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)p->fb, Cp, (float *)grid,
-                               p->npts, nfields, G, p->T, p->Jp);
+                                       (const float2 *)p->kern, (const float *)p->fb, Cp, (float *)grid, p->npts,
+                                       nfields, G, p->max_fft_smem, p->T, p->Jp);
     }
     ST_CUDA(cudaGetLastError());
     return ST_OK;

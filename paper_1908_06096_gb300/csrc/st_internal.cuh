@@ -57,8 +57,9 @@ struct RowPair {
     int M;                    // wavenumbers kept: 0..M
     int mode;                 // 0 direct mixed radix, 1 Bluestein
     int fftlen;               // length of the FFTs run: N (mode 0) or L (mode 1)
-    int nrad;                 // number of Stockham passes of length fftlen
-    int rad[MAX_RADICES];     // radix of each pass
+    int nrad;                 // number of radix stages of length fftlen
+    int rad[MAX_RADICES];     // radix of each stage (decimation-in-frequency order)
+    int swz;                  // shared-memory address map (see fft_swz)
     long long tw_off;         // first of the row's fftlen roots of unity e^{-2 pi i t / fftlen}
     long long chirp_off;      // mode 1: N chirp values w_k = e^{-i pi k^2 / N}
     long long kern_off;       // mode 1: L values FFT_L(b) / L, b the conjugate chirp wrapped circularly
@@ -70,6 +71,40 @@ struct RowPair {
 // in one direction.  out[col][c] = sum_r tab[col][r] * data[r][c].
 //   inverse: col = northern row j (ncol = J), r = k with n = m + p + 2k
 //   direct:  col = k (ncol = K_m^p), r = northern row j (K = J)
+// Place of frequency m after in-place decimation-in-frequency passes over
+// the radices rad[0..nrad) of L: m = d1 + R1 (d2 + R2 (...)), place =
+// sum_s d_s L / (R1 ... Rs) (the mixed-radix digit reversal).
+__host__ __device__ inline int dif_pos(int m, const RowPair &rp)
+{
+    int pos = 0, stride = rp.fftlen;
+    for (int q = 0; q < rp.nrad; ++q) {
+        const int R = rp.rad[q];
+        const int d = m % R;
+        m /= R;
+        stride /= R;
+        pos += d * stride;
+    }
+    return pos;
+}
+
+// Shared-memory address of FFT element i for a row's address map: 0 plain,
+// 1 one pad slot per 16, 2 one pad slot per 32, 3 XOR of bits 4-7 into bits
+// 0-3.  The plan picks, per row, the map with the fewest bank conflicts over
+// that row's passes.
+__host__ __device__ inline int fft_swz(int i, int mode)
+{
+    switch (mode) {
+    case 1: return i + (i >> 4);
+    case 2: return i + (i >> 5);
+    case 3: return i ^ ((i >> 4) & 15);
+    default: return i;
+    }
+}
+__host__ __device__ inline int fft_swz_size(int L, int mode)
+{
+    return mode == 1 ? L + (L >> 4) + 1 : (mode == 2 ? L + (L >> 5) + 1 : L);
+}
+
 struct LegGroup {
     int m, p;
     int ncol;                 // valid columns of the table
@@ -118,6 +153,7 @@ struct st_plan {
     long long nchirp = 0, nkern = 0;
     int max_row = 0;                     // largest N
     int max_fft = 0;                     // largest fftlen
+    int max_fft_smem = 0;                // largest shared-memory slot (fftlen after padding)
     int max_chirp = 0;                   // largest N among Bluestein rows
 
     // Legendre data, [0] inverse, [1] direct

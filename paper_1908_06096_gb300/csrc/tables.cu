@@ -318,12 +318,14 @@ __global__ void k_bluestein_kern(const RowPair *rps, int J, double2 *scratch, lo
         y = t;
         Lc *= R;
     }
+    // stored in the digit-reversed order the runtime DIF passes leave their
+    // output in, so the pointwise product needs no permutation
     const double inv = 1.0 / (double)L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         C v;
         v.x = (decltype(v.x))(x[i].x * inv);
         v.y = (decltype(v.y))(x[i].y * inv);
-        kern[r.kern_off + i] = v;
+        kern[r.kern_off + dif_pos(i, r)] = v;
     }
 }
 
