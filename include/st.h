@@ -143,6 +143,33 @@ st_status st_inv_trans(st_plan_t plan, const void *spec_dev, void *grid_dev, int
 st_status st_dir_trans(st_plan_t plan, const void *grid_dev, void *spec_dev, int nfields,
                        void *stream);
 
+/*
+ * Inverse transform exactly like st_inv_trans, but its scratch (the packed
+ * spectral operand and the Fourier buffer) lives in one fixed array compiled
+ * into the library (st_static_scratch_bytes() bytes, 32 MiB) instead of the
+ * plan's workspace.  The paper has no counterpart: it is for callers that
+ * must not allocate device memory where they run the transform -- work
+ * recorded during a global-mode stream capture, real-time loops where an
+ * allocation may stall, frameworks that own all device memory -- and it calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *  - Returns ST_ERR_ARG (message in st_last_error) when the plan and
+ *    `nfields` need more scratch than the array holds; nfields may exceed the
+ *    plan's max_fields as long as the scratch suffices.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and it keeps the last
+ *    call's contents; the call clears what must start at zero itself.  Calls
+ *    that can overlap on the GPU (other streams, or the same array used from
+ *    several host threads without ordering) race on it and give wrong results.
+ *  - Every GPU that loads the library holds the array until the process exits.
+ */
+st_status st_inv_trans_static(st_plan_t plan, const void *spec_dev, void *grid_dev, int nfields,
+                              void *stream);
+
+/* Size in bytes of the array st_inv_trans_static uses. */
+size_t st_static_scratch_bytes(void);
+
 /* Wait for the plan's work on `stream` and report any device-side error
  * recorded since the last call (then clear it). */
 st_status st_plan_sync(st_plan_t plan, void *stream);

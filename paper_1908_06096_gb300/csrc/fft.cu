@@ -628,8 +628,9 @@ st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t
     return ST_OK;
 }
 
-st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s)
+st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb_in)
 {
+    const void *fb = fb_in ? fb_in : p->fb;
     size_t smem;
     int G = fft_fields_per_cta(p, nfields, &smem);
     if (smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
@@ -640,13 +641,13 @@ st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s)
         auto k = k_fft_inv<double>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double2 *)p->chirp,
-                                       (const double2 *)p->kern, (const double *)p->fb, Cp, (double *)grid, p->npts,
+                                       (const double2 *)p->kern, (const double *)fb, Cp, (double *)grid, p->npts,
                                        nfields, G, p->max_fft_smem, p->T, p->Jp);
     } else {
         auto k = k_fft_inv<float>;
         if ((r = set_smem(k, smem))) return r;
         k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)p->fb, Cp, (float *)grid, p->npts,
+                                       (const float2 *)p->kern, (const float *)fb, Cp, (float *)grid, p->npts,
                                        nfields, G, p->max_fft_smem, p->T, p->Jp);
     }
     ST_CUDA(cudaGetLastError());

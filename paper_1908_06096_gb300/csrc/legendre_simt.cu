@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) k_leg_simt(const LegGroup *__restrict__ g
     }
 }
 
-st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s)
+st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s, void *data_in, void *out_in)
 {
     int C = 2 * nfields, Cp = cols_padded(nfields);
     int ncm = (C + SIMT_TILE - 1) / SIMT_TILE;
@@ -84,8 +84,8 @@ st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s)
     if (nt == 0) return ST_OK;
     if (nt > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
     // inverse: data = packed spectra, out = Fourier buffer; direct: the reverse
-    void *data = dir == 0 ? p->sop : p->fbop;
-    void *out = dir == 0 ? p->fb : p->sout;
+    void *data = data_in ? data_in : (dir == 0 ? p->sop : p->fbop);
+    void *out = out_in ? out_in : (dir == 0 ? p->fb : p->sout);
     if (p->prec == P_FP64)
         k_leg_simt<double><<<(unsigned)nt, 256, 0, s>>>(p->groups[dir], p->tiles[dir], ncm, (const double *)p->tab[dir],
                                                         (const double *)data, (double *)out, C, Cp);
@@ -207,24 +207,25 @@ __global__ void __launch_bounds__(256) k_unpack(int T, int max_m, const long lon
     }
 }
 
-st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s)
+st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s, void *sop_in)
 {
+    void *sop = sop_in ? sop_in : p->sop;
     int Cp = cols_padded(nfields);
     const long long Rp = p->srow_total;
     long long ps = Rp * Cp;
     dim3 g((nfields + 31) / 32, p->max_m + 1);
     switch (p->prec) {
     case P_FP64:
-        k_pack<double, S_F64><<<g, 256, 0, s>>>(p->T, (const double *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
+        k_pack<double, S_F64><<<g, 256, 0, s>>>(p->T, (const double *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
         break;
     case P_FP32:
-        k_pack<float, S_F32><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
+        k_pack<float, S_F32><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
         break;
     case P_TF32X3:
-        k_pack<float, S_TF32_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
+        k_pack<float, S_TF32_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
         break;
     default:
-        k_pack<float, S_BF16_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, p->sop, Cp, Rp, ps);
+        k_pack<float, S_BF16_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
         break;
     }
     ST_CUDA(cudaGetLastError());

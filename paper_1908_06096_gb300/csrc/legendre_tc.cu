@@ -479,15 +479,15 @@ size_t tc_smem_bytes(int prec, int max_nt, int *stages_out)
     return 1024 + (size_t)S * stage + ctrl;
 }
 
-st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s)
+st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s, void *data_in, void *out_in)
 {
     const int C = 2 * nfields, Cp = cols_padded(nfields);
     const int ncm = (C + TC_M - 1) / TC_M;
     const long long total = (long long)p->ntiles[dir] * ncm;
     if (total == 0) return ST_OK;
     const bool bf16 = p->prec == P_BF16X3;
-    void *data = dir == 0 ? p->sop : p->fbop;
-    void *out = dir == 0 ? p->fb : p->sout;
+    void *data = data_in ? data_in : (dir == 0 ? p->sop : p->fbop);
+    void *out = out_in ? out_in : (dir == 0 ? p->fb : p->sout);
     const long long rows = dir == 0 ? p->srow_total : fb_rows(p);
     CUtensorMap map;
     st_status r = make_operand_map(&map, data, bf16, C, rows, Cp);

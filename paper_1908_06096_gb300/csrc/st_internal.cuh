@@ -224,11 +224,14 @@ st_status launch_tables(st_plan *p, cudaStream_t s);
 st_status launch_twiddles(st_plan *p, cudaStream_t s);
 st_status launch_bluestein_setup(st_plan *p, cudaStream_t s);
 st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s);
-st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s);
-st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s);
+// The optional buffer arguments below replace the plan's own workspace
+// buffers for one call (nullptr: use the plan's).
+st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb = nullptr);
+st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s, void *sop = nullptr);
 st_status launch_unpack(st_plan *p, void *spec, int nfields, cudaStream_t s);
-st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s);
-st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s);
+st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s, void *data = nullptr,
+                          void *out = nullptr);
+st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s, void *data = nullptr, void *out = nullptr);
 st_status launch_fourier_export(st_plan *p, int dir, int nfields, double *out, cudaStream_t s);
 st_status launch_gauss(int nlat, double *mu, double *w, cudaStream_t s);
 st_status launch_legendre_values(int T, const double *mu, int nmu, double *out, cudaStream_t s);

@@ -71,6 +71,8 @@ SIGNATURES = {
     "st_plan_set_timing": [_VP, _I],
     "st_plan_timings": [_VP, ctypes.POINTER(_KernelTime), _I, ctypes.POINTER(ctypes.c_int)],
     "st_plan_reset_timings": [_VP],
+    "st_inv_trans_static": [_VP, _VP, _VP, _I, _VP],
+    "st_static_scratch_bytes": [],
 }
 
 
@@ -93,6 +95,7 @@ def load():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.st_static_scratch_bytes.restype = ctypes.c_size_t
     lib.st_status_string.restype = ctypes.c_char_p
     lib.st_last_error.restype = ctypes.c_char_p
     _lib = lib
@@ -201,6 +204,16 @@ class Plan:
         if out is None:
             out = torch.empty((nf, self.npts), dtype=self.dtype, device=spec.device)
         _check(load().st_inv_trans(self._h, _ptr(spec), _ptr(out), nf, _stream_handle(stream)), "st_inv_trans")
+        return out
+
+    def inv_static(self, spec: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Inverse transform through st_inv_trans_static (scratch in the
+        library's fixed device array; no allocation inside the call)."""
+        nf = self._nf(spec, self.nspec * 2)
+        if out is None:
+            out = torch.empty((nf, self.npts), dtype=self.dtype, device=spec.device)
+        _check(load().st_inv_trans_static(self._h, _ptr(spec), _ptr(out), nf, _stream_handle(stream)),
+               "st_inv_trans_static")
         return out
 
     def dir(self, grid: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

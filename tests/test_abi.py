@@ -16,7 +16,7 @@ def _declared():
         with open(os.path.join(ROOT, "include", h)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(?:st_status|const\s+char\s*\*)\s*(st_\w+)\s*\(", text):
+        for m in re.finditer(r"\b(?:st_status|const\s+char\s*\*|size_t)\s*(st_\w+)\s*\(", text):
             names.add(m.group(1))
     return names
 
