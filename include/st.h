@@ -175,6 +175,40 @@ size_t st_static_scratch_bytes(void);
 st_status st_plan_sync(st_plan_t plan, void *stream);
 
 /*
+ * Batched transforms of many plans at once (ESCAPE D3.3 sections 4.2.3-4.2.5:
+ * fewer, larger kernels instead of many small library calls; here across
+ * requests of different truncations and grids as well as across m and rows).
+ * A batch is built once from a list of items; st_batch_run then issues one
+ * launch per stage for all items (spectral pack, Legendre, FFT, and the same
+ * for the direct direction), optionally recorded once into a CUDA graph and
+ * replayed on later runs.
+ *  direction 0: inverse, spec_in -> grid
+ *  direction 1: direct, grid -> spec_out
+ *  direction 2: round trip, spec_in -> grid -> spec_out
+ * Every pointer is a device pointer the caller owns and keeps alive while
+ * the batch exists.  A plan may appear in at most one item of a batch
+ * (ST_ERR_BUSY otherwise); nfields must lie in [1, the plan's max_fields].
+ * Items are grouped by precision; at most 64 items of one precision run in
+ * one launch (larger groups take several).
+ */
+typedef struct st_batch *st_batch_t;
+
+typedef struct {
+    st_plan_t plan;
+    int direction;
+    const void *spec_in;
+    void *grid;
+    void *spec_out;
+    int nfields;
+} st_batch_item;
+
+st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n);
+/* use_graph != 0: the first run records the launches into a CUDA graph on
+ * `stream` and every run replays it (the stream must not be capturing). */
+st_status st_batch_run(st_batch_t batch, void *stream, int use_graph);
+st_status st_batch_destroy(st_batch_t batch);
+
+/*
  * Per-kernel timing (not in the paper; a measurement aid).  While enabled,
  * every kernel the plan launches is bracketed by two CUDA events recorded on
  * its launch stream; st_plan_timings waits for them and reports, per kernel,

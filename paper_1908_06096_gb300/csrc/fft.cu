@@ -418,22 +418,25 @@ __device__ inline void store_pair(void *base, long long r, int c, int Cp, long l
 template <typename Rr> struct FftBounds { static constexpr int MINB = 3; };
 template <> struct FftBounds<double> { static constexpr int MINB = 1; };
 
-template <typename Rr, int S>
-__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
-    k_fft_dir(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
-              const typename CT<Rr>::T *__restrict__ chirp_all, const typename CT<Rr>::T *__restrict__ kern_all,
-              const Rr *__restrict__ grid, long long npts, int nfields, int G, int Sslot, void *fb, int Cp,
-              long long Rp, long long plane_stride, int T, int Jp)
+template <typename Rr, int S, int MAXJ>
+__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_dir(const __grid_constant__ FftBatch<MAXJ> B)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int j = blockIdx.y;
-    const RowPair rp = rps[j];
-    const int N = rp.N, W = rp.fftlen, SL = Sslot;
+    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
+    const FftJob &J = B.job[q];
+    const int b = (int)(blockIdx.x - B.prefix[q]);
+    const int j = b / J.nfg, G = J.G;
+    const int f0 = (b - j * J.nfg) * G;
+    const RowPair rp = J.rps[j];
+    const int N = rp.N, W = rp.fftlen, SL = J.Sslot;
+    const int nfields = J.nfields, Cp = J.Cp, T = J.T, Jp = J.Jp;
+    const long long npts = J.npts, Rp = J.Rp, plane_stride = J.ps;
+    const Rr *grid = (const Rr *)J.src;
+    void *fb = J.dst;
     C *x = (C *)smem_raw;
-    const C *tw = tw_all + rp.tw_off;
-    const C *chirp = chirp_all + rp.chirp_off;
-    const int f0 = blockIdx.x * G;
+    const C *tw = (const C *)J.tw + rp.tw_off;
+    const C *chirp = (const C *)J.chirp + rp.chirp_off;
     const Swz sw(rp.swz);
 
     const FastDiv dW(W);
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
         x[(size_t)f * SL + sw(k)] = v;
     }
     __syncthreads();
-    fft_forward<C>(x, tw, kern_all + rp.kern_off, rp, G, SL);
+    fft_forward<C>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, SL);
 
     const Rr inv = (Rr)1.0 / (Rr)N;
     const int M = rp.M;
@@ -477,22 +480,26 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
     }
 }
 
-template <typename Rr>
-__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
-    k_fft_inv(const RowPair *__restrict__ rps, const typename CT<Rr>::T *__restrict__ tw_all,
-              const typename CT<Rr>::T *__restrict__ chirp_all, const typename CT<Rr>::T *__restrict__ kern_all,
-              const Rr *__restrict__ fb, int Cp, Rr *__restrict__ grid, long long npts, int nfields, int G,
-              int Sslot, int T, int Jp)
+template <typename Rr, int MAXJ>
+__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_inv(const __grid_constant__ FftBatch<MAXJ> B)
 {
     typedef typename CT<Rr>::T C;
+    typedef typename CT<Rr>::T C2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int j = blockIdx.y;
-    const RowPair rp = rps[j];
-    const int N = rp.N, S = Sslot;
+    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
+    const FftJob &J = B.job[q];
+    const int b = (int)(blockIdx.x - B.prefix[q]);
+    const int j = b / J.nfg, G = J.G;
+    const int f0 = (b - j * J.nfg) * G;
+    const RowPair rp = J.rps[j];
+    const int N = rp.N, S = J.Sslot;
+    const int nfields = J.nfields, Cp = J.Cp, T = J.T, Jp = J.Jp;
+    const long long npts = J.npts;
+    const Rr *fb = (const Rr *)J.src;
+    Rr *grid = (Rr *)J.dst;
     C *x = (C *)smem_raw;
-    const C *tw = tw_all + rp.tw_off;
-    const C *chirp = chirp_all + rp.chirp_off;
-    const int f0 = blockIdx.x * G;
+    const C *tw = (const C *)J.tw + rp.tw_off;
+    const C *chirp = (const C *)J.chirp + rp.chirp_off;
     const Swz sw(rp.swz);
 
     for (int idx = threadIdx.x; idx < G * S; idx += blockDim.x) {
@@ -504,7 +511,6 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
     __syncthreads();
     // conj(Z): Z[m] = Xn + i Xs, Z[N-m] = conj(Xn) + i conj(Xs), Z[0] = Re Xn + i Re Xs,
     // times the chirp at the same place for Bluestein rows
-    typedef typename CT<Rr>::T C2;
     const int M = rp.M;
     const FastDiv dG(G);
     for (int idx = threadIdx.x; idx < (M + 1) * G; idx += blockDim.x) {
@@ -531,21 +537,21 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB)
             if (rp.mode == 1) v = cmul(v, __ldg(&chirp[0]));
             xf[sw(0)] = v;
         } else {
-            C a, b;
+            C a, bb;
             a.x = nx - qy;
             a.y = -(ny + qx);
-            b.x = nx + qy;
-            b.y = ny - qx;
+            bb.x = nx + qy;
+            bb.y = ny - qx;
             if (rp.mode == 1) {
                 a = cmul(a, __ldg(&chirp[m]));
-                b = cmul(b, __ldg(&chirp[N - m]));
+                bb = cmul(bb, __ldg(&chirp[N - m]));
             }
             xf[sw(m)] = a;
-            xf[sw(N - m)] = b;
+            xf[sw(N - m)] = bb;
         }
     }
     __syncthreads();
-    fft_forward<C>(x, tw, kern_all + rp.kern_off, rp, G, S);
+    fft_forward<C>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, S);
     const FastDiv dN(N);
     for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
         const int f = dN(idx), k = idx - f * N;
@@ -580,78 +586,92 @@ static st_status set_smem(K kern, size_t smem)
     return ST_OK;
 }
 
-st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s)
+st_status fft_job(st_plan *p, int dir, int nfields, const void *src, void *dst, FftJob *job, size_t *smem)
 {
-    size_t smem;
-    int G = fft_fields_per_cta(p, nfields, &smem);
-    if (smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
-    dim3 g((nfields + G - 1) / G, p->J);
-    int Cp = cols_padded(nfields);
-    const long long Rp = fb_rows(p);
-    const long long ps = Rp * Cp;
-    st_status r = ST_OK;
-    switch (p->prec) {
-    case P_FP64: {
-        auto k = k_fft_dir<double, S_F64>;
-        if ((r = set_smem(k, smem))) return r;
-        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double2 *)p->chirp,
-                                       (const double2 *)p->kern, (const double *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop,
-                                       Cp, Rp, ps, p->T, p->Jp);
-        break;
+    FftJob &J = *job;
+    J.rps = p->rowpairs;
+    J.tw = p->tw;
+    J.chirp = p->chirp;
+    J.kern = p->kern;
+    J.src = src;
+    J.dst = dst;
+    J.npts = p->npts;
+    J.nfields = nfields;
+    J.G = fft_fields_per_cta(p, nfields, smem);
+    J.Sslot = p->max_fft_smem;
+    J.Cp = cols_padded(nfields);
+    J.Rp = fb_rows(p);
+    J.ps = J.Rp * J.Cp;
+    J.T = p->T;
+    J.Jp = p->Jp;
+    J.J = p->J;
+    J.nfg = (nfields + J.G - 1) / J.G;
+    if (*smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
+    return ST_OK;
+}
+
+template <int MAXJ, class K>
+static st_status run_fft_batch(K kern, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
+{
+    FftBatch<MAXJ> B;
+    B.njobs = n;
+    long long tot = 0;
+    for (int q = 0; q < n; ++q) {
+        B.prefix[q] = tot;
+        B.job[q] = jobs[q];
+        tot += (long long)jobs[q].J * jobs[q].nfg;
     }
-    case P_FP32: {
-        auto k = k_fft_dir<float, S_F32>;
-        if ((r = set_smem(k, smem))) return r;
-        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop, Cp,
-                                       Rp, ps, p->T, p->Jp);
-        break;
-    }
-    case P_TF32X3: {
-        auto k = k_fft_dir<float, S_TF32_SPLIT>;
-        if ((r = set_smem(k, smem))) return r;
-        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop, Cp,
-                                       Rp, ps, p->T, p->Jp);
-        break;
-    }
-    default: {
-        auto k = k_fft_dir<float, S_BF16_SPLIT>;
-        if ((r = set_smem(k, smem))) return r;
-        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)grid, p->npts, nfields, G, p->max_fft_smem, p->fbop, Cp,
-                                       Rp, ps, p->T, p->Jp);
-        break;
-    }
-    }
+    B.prefix[n] = tot;
+    if (tot == 0) return ST_OK;
+    if (tot > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
+    st_status r = set_smem(kern, smem);
+    if (r) return r;
+    kern<<<(unsigned)tot, FFT_THREADS, smem, s>>>(B);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }
 
+template <int MAXJ>
+static st_status launch_fft_jobs_t(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
+{
+    if (dir == 1) {
+        switch (prec) {
+        case P_FP64: return run_fft_batch<MAXJ>(k_fft_dir<double, S_F64, MAXJ>, jobs, n, smem, s);
+        case P_FP32: return run_fft_batch<MAXJ>(k_fft_dir<float, S_F32, MAXJ>, jobs, n, smem, s);
+        case P_TF32X3: return run_fft_batch<MAXJ>(k_fft_dir<float, S_TF32_SPLIT, MAXJ>, jobs, n, smem, s);
+        default: return run_fft_batch<MAXJ>(k_fft_dir<float, S_BF16_SPLIT, MAXJ>, jobs, n, smem, s);
+        }
+    }
+    if (prec == P_FP64) return run_fft_batch<MAXJ>(k_fft_inv<double, MAXJ>, jobs, n, smem, s);
+    return run_fft_batch<MAXJ>(k_fft_inv<float, MAXJ>, jobs, n, smem, s);
+}
+
+// dir 0: inverse (Fourier buffer -> grid), 1: direct (grid -> operand).  All
+// jobs share the precision `prec`; smem is the largest any job needs.
+st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
+{
+    if (n <= 0) return ST_OK;
+    if (n == 1) return launch_fft_jobs_t<1>(dir, prec, jobs, n, smem, s);
+    if (n > MAX_JOBS) return ST_ERR_ARG;
+    return launch_fft_jobs_t<MAX_JOBS>(dir, prec, jobs, n, smem, s);
+}
+
+st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s)
+{
+    FftJob J;
+    size_t smem = 0;
+    st_status r = fft_job(p, 1, nfields, grid, p->fbop, &J, &smem);
+    if (r) return r;
+    return launch_fft_jobs(1, p->prec, &J, 1, smem, s);
+}
+
 st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb_in)
 {
-    const void *fb = fb_in ? fb_in : p->fb;
-    size_t smem;
-    int G = fft_fields_per_cta(p, nfields, &smem);
-    if (smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
-    dim3 g((nfields + G - 1) / G, p->J);
-    int Cp = cols_padded(nfields);
-    st_status r = ST_OK;
-    if (p->prec == P_FP64) {
-        auto k = k_fft_inv<double>;
-        if ((r = set_smem(k, smem))) return r;
-        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const double2 *)p->tw, (const double2 *)p->chirp,
-                                       (const double2 *)p->kern, (const double *)fb, Cp, (double *)grid, p->npts,
-                                       nfields, G, p->max_fft_smem, p->T, p->Jp);
-    } else {
-        auto k = k_fft_inv<float>;
-        if ((r = set_smem(k, smem))) return r;
-        k<<<g, FFT_THREADS, smem, s>>>(p->rowpairs, (const float2 *)p->tw, (const float2 *)p->chirp,
-                                       (const float2 *)p->kern, (const float *)fb, Cp, (float *)grid, p->npts,
-                                       nfields, G, p->max_fft_smem, p->T, p->Jp);
-    }
-    ST_CUDA(cudaGetLastError());
-    return ST_OK;
+    FftJob J;
+    size_t smem = 0;
+    st_status r = fft_job(p, 0, nfields, fb_in ? fb_in : p->fb, grid, &J, &smem);
+    if (r) return r;
+    return launch_fft_jobs(0, p->prec, &J, 1, smem, s);
 }
 
 }  // namespace st

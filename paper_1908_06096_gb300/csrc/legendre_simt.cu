@@ -16,18 +16,22 @@ namespace st {
 
 // out[col][c] = sum_r tab[col][r] * data[r][c] for one (group, column tile,
 // data tile) per CTA; 64 x 64 outputs, 256 threads with 4 x 4 each.
-template <typename Rr>
-__global__ void __launch_bounds__(256) k_leg_simt(const LegGroup *__restrict__ groups, const LegTile *__restrict__ tiles,
-                                                  int ncm, const Rr *__restrict__ tab, const Rr *__restrict__ data,
-                                                  Rr *__restrict__ out, int C, int Cp)
+template <typename Rr, int MAXJ>
+__global__ void __launch_bounds__(256) k_leg_simt(const __grid_constant__ SimtBatch<MAXJ> B)
 {
     constexpr int TB = SIMT_TILE, KB = 16;
     __shared__ Rr As[KB][TB + 1];
     __shared__ Rr Bs[KB][TB];
-    const int tile = blockIdx.x;
-    const LegTile lt = tiles[tile / ncm];
+    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
+    const SimtJob &J = B.job[q];
+    const int tile = (int)(blockIdx.x - B.prefix[q]);
+    const int ncm = J.ncm, C = J.C, Cp = J.Cp;
+    const LegTile lt = J.tiles[tile / ncm];
     const int cm = tile % ncm;
-    const LegGroup g = groups[lt.g];
+    const LegGroup g = J.groups[lt.g];
+    const Rr *tab = (const Rr *)J.tab;
+    const Rr *data = (const Rr *)J.data;
+    Rr *out = (Rr *)J.out;
     const int col0 = lt.ct * TB, c0 = cm * TB;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     Rr acc[4][4];
@@ -53,9 +57,9 @@ __global__ void __launch_bounds__(256) k_leg_simt(const LegGroup *__restrict__ g
         for (int kk = 0; kk < KB; ++kk) {
             Rr a[4], b[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) a[q] = As[kk][ty * 4 + q];
+            for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) b[q] = Bs[kk][tx * 4 + q];
+            for (int u = 0; u < 4; ++u) b[u] = Bs[kk][tx * 4 + u];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -76,24 +80,59 @@ __global__ void __launch_bounds__(256) k_leg_simt(const LegGroup *__restrict__ g
     }
 }
 
+st_status simt_job(st_plan *p, int dir, int nfields, const void *data, void *out, SimtJob *job, long long *blocks)
+{
+    job->groups = p->groups[dir];
+    job->tiles = p->tiles[dir];
+    job->tab = p->tab[dir];
+    job->data = data;
+    job->out = out;
+    job->C = 2 * nfields;
+    job->Cp = cols_padded(nfields);
+    job->ncm = (job->C + SIMT_TILE - 1) / SIMT_TILE;
+    *blocks = (long long)p->ntiles[dir] * job->ncm;
+    return ST_OK;
+}
+
+template <int MAXJ, class K>
+static st_status run_simt_batch(K kern, const SimtJob *jobs, const long long *blocks, int n, cudaStream_t s)
+{
+    SimtBatch<MAXJ> B;
+    B.njobs = n;
+    long long tot = 0;
+    for (int q = 0; q < n; ++q) {
+        B.prefix[q] = tot;
+        B.job[q] = jobs[q];
+        tot += blocks[q];
+    }
+    B.prefix[n] = tot;
+    if (tot == 0) return ST_OK;
+    if (tot > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
+    kern<<<(unsigned)tot, 256, 0, s>>>(B);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+st_status launch_simt_jobs(int prec, const SimtJob *jobs, const long long *blocks, int n, cudaStream_t s)
+{
+    if (n <= 0) return ST_OK;
+    if (n > MAX_JOBS) return ST_ERR_ARG;
+    if (n == 1)
+        return prec == P_FP64 ? run_simt_batch<1>(k_leg_simt<double, 1>, jobs, blocks, n, s)
+                              : run_simt_batch<1>(k_leg_simt<float, 1>, jobs, blocks, n, s);
+    return prec == P_FP64 ? run_simt_batch<MAX_JOBS>(k_leg_simt<double, MAX_JOBS>, jobs, blocks, n, s)
+                          : run_simt_batch<MAX_JOBS>(k_leg_simt<float, MAX_JOBS>, jobs, blocks, n, s);
+}
+
 st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s, void *data_in, void *out_in)
 {
-    int C = 2 * nfields, Cp = cols_padded(nfields);
-    int ncm = (C + SIMT_TILE - 1) / SIMT_TILE;
-    long long nt = (long long)p->ntiles[dir] * ncm;
-    if (nt == 0) return ST_OK;
-    if (nt > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
     // inverse: data = packed spectra, out = Fourier buffer; direct: the reverse
     void *data = data_in ? data_in : (dir == 0 ? p->sop : p->fbop);
     void *out = out_in ? out_in : (dir == 0 ? p->fb : p->sout);
-    if (p->prec == P_FP64)
-        k_leg_simt<double><<<(unsigned)nt, 256, 0, s>>>(p->groups[dir], p->tiles[dir], ncm, (const double *)p->tab[dir],
-                                                        (const double *)data, (double *)out, C, Cp);
-    else
-        k_leg_simt<float><<<(unsigned)nt, 256, 0, s>>>(p->groups[dir], p->tiles[dir], ncm, (const float *)p->tab[dir],
-                                                       (const float *)data, (float *)out, C, Cp);
-    ST_CUDA(cudaGetLastError());
-    return ST_OK;
+    SimtJob J;
+    long long blocks = 0;
+    simt_job(p, dir, nfields, data, out, &J, &blocks);
+    return launch_simt_jobs(p->prec, &J, &blocks, 1, s);
 }
 
 // ---------------------------------------------------------------- pack / unpack
@@ -128,17 +167,22 @@ __device__ inline void put_op(void *base, long long idx, long long ps, Rr v)
 // Spectra [field][(m,n)][re,im] -> operand rows: (m, n) with n - m = 2k + p
 // goes to row srow[2m + p] + k (the even half, then the odd half of each m);
 // column 2 f + (re, im).  One CTA per (m, 32-field tile); smem transpose.
-template <typename Rr, int S>
-__global__ void __launch_bounds__(256) k_pack(int T, const Rr *__restrict__ spec, int nfields, long long nspec,
-                                              const long long *__restrict__ srow, void *out, int Cp, long long Rp,
-                                              long long ps)
+template <typename Rr, int S, int MAXJ>
+__global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackBatch<MAXJ> B)
 {
     __shared__ Rr tile[32][65];
-    const int m = blockIdx.y;
-    const int f0 = blockIdx.x * 32;
+    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
+    const PackJob &J = B.job[q];
+    const int b = (int)(blockIdx.x - B.prefix[q]);
+    const int m = b / J.nft;
+    const int f0 = (b - m * J.nft) * 32;
+    const int T = J.T, nfields = J.nfields, Cp = J.Cp;
+    const long long nspec = J.nspec, Rp = J.Rp, ps = J.ps;
+    const Rr *spec = (const Rr *)J.src;
+    void *out = J.dst;
     const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
     const int len = T - m + 1;
-    const long long rowE = srow[2 * m], rowO = srow[2 * m + 1];
+    const long long rowE = J.srow[2 * m], rowO = J.srow[2 * m + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d0 = 0; d0 < len; d0 += 32) {
         // load: warp w reads fields w, w+8, ...; lane = d
@@ -170,19 +214,24 @@ __global__ void __launch_bounds__(256) k_pack(int T, const Rr *__restrict__ spec
 
 // Operand rows (direct GEMM output, FP32/FP64) -> spectra.  Wavenumbers kept
 // by no row (m > max_m) are written as zero; Im a_n^0 is written as zero.
-template <typename Rr>
-__global__ void __launch_bounds__(256) k_unpack(int T, int max_m, const long long *__restrict__ srow,
-                                                const Rr *__restrict__ in, int Cp, int nfields, long long nspec,
-                                                Rr *__restrict__ spec)
+template <typename Rr, int MAXJ>
+__global__ void __launch_bounds__(256) k_unpack(const __grid_constant__ PackBatch<MAXJ> B)
 {
     __shared__ Rr tile[32][65];
-    const int m = blockIdx.y;
-    const int f0 = blockIdx.x * 32;
+    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
+    const PackJob &J = B.job[q];
+    const int b = (int)(blockIdx.x - B.prefix[q]);
+    const int m = b / J.nft;
+    const int f0 = (b - m * J.nft) * 32;
+    const int T = J.T, nfields = J.nfields, Cp = J.Cp;
+    const long long nspec = J.nspec;
+    const Rr *in = (const Rr *)J.src;
+    Rr *spec = (Rr *)J.dst;
     const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
     const int len = T - m + 1;
-    const long long rowE = srow[2 * m], rowO = srow[2 * m + 1];
+    const long long rowE = J.srow[2 * m], rowO = J.srow[2 * m + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool zero = m > max_m;
+    const bool zero = m > J.max_m;
     for (int d0 = 0; d0 < len; d0 += 32) {
         for (int dd = warp; dd < 32; dd += 8) {
             int d = d0 + dd;
@@ -207,43 +256,77 @@ __global__ void __launch_bounds__(256) k_unpack(int T, int max_m, const long lon
     }
 }
 
-st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s, void *sop_in)
+// dir 0: pack (spectra -> operand), 1: unpack (GEMM output -> spectra).
+st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job)
 {
-    void *sop = sop_in ? sop_in : p->sop;
-    int Cp = cols_padded(nfields);
-    const long long Rp = p->srow_total;
-    long long ps = Rp * Cp;
-    dim3 g((nfields + 31) / 32, p->max_m + 1);
-    switch (p->prec) {
-    case P_FP64:
-        k_pack<double, S_F64><<<g, 256, 0, s>>>(p->T, (const double *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
-        break;
-    case P_FP32:
-        k_pack<float, S_F32><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
-        break;
-    case P_TF32X3:
-        k_pack<float, S_TF32_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
-        break;
-    default:
-        k_pack<float, S_BF16_SPLIT><<<g, 256, 0, s>>>(p->T, (const float *)spec, nfields, p->nspec, p->srow, sop, Cp, Rp, ps);
-        break;
+    PackJob &J = *job;
+    J.src = src;
+    J.dst = dst;
+    J.srow = p->srow;
+    J.nspec = p->nspec;
+    J.Cp = cols_padded(nfields);
+    J.Rp = p->srow_total;
+    J.ps = J.Rp * J.Cp;
+    J.T = p->T;
+    J.max_m = p->max_m;
+    J.nfields = nfields;
+    J.nft = (nfields + 31) / 32;
+    J.nm = dir == 0 ? p->max_m + 1 : p->T + 1;
+    return ST_OK;
+}
+
+template <int MAXJ, class K>
+static st_status run_pack_batch(K kern, const PackJob *jobs, int n, cudaStream_t s)
+{
+    PackBatch<MAXJ> B;
+    B.njobs = n;
+    long long tot = 0;
+    for (int q = 0; q < n; ++q) {
+        B.prefix[q] = tot;
+        B.job[q] = jobs[q];
+        tot += (long long)jobs[q].nm * jobs[q].nft;
     }
+    B.prefix[n] = tot;
+    if (tot == 0) return ST_OK;
+    kern<<<(unsigned)tot, 256, 0, s>>>(B);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }
 
+template <int MAXJ>
+static st_status launch_pack_jobs_t(int dir, int prec, const PackJob *jobs, int n, cudaStream_t s)
+{
+    if (dir == 1)
+        return prec == P_FP64 ? run_pack_batch<MAXJ>(k_unpack<double, MAXJ>, jobs, n, s)
+                              : run_pack_batch<MAXJ>(k_unpack<float, MAXJ>, jobs, n, s);
+    switch (prec) {
+    case P_FP64: return run_pack_batch<MAXJ>(k_pack<double, S_F64, MAXJ>, jobs, n, s);
+    case P_FP32: return run_pack_batch<MAXJ>(k_pack<float, S_F32, MAXJ>, jobs, n, s);
+    case P_TF32X3: return run_pack_batch<MAXJ>(k_pack<float, S_TF32_SPLIT, MAXJ>, jobs, n, s);
+    default: return run_pack_batch<MAXJ>(k_pack<float, S_BF16_SPLIT, MAXJ>, jobs, n, s);
+    }
+}
+
+st_status launch_pack_jobs(int dir, int prec, const PackJob *jobs, int n, cudaStream_t s)
+{
+    if (n <= 0) return ST_OK;
+    if (n > MAX_JOBS) return ST_ERR_ARG;
+    if (n == 1) return launch_pack_jobs_t<1>(dir, prec, jobs, n, s);
+    return launch_pack_jobs_t<MAX_JOBS>(dir, prec, jobs, n, s);
+}
+
+st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s, void *sop_in)
+{
+    PackJob J;
+    pack_job(p, 0, nfields, spec, sop_in ? sop_in : p->sop, &J);
+    return launch_pack_jobs(0, p->prec, &J, 1, s);
+}
+
 st_status launch_unpack(st_plan *p, void *spec, int nfields, cudaStream_t s)
 {
-    int Cp = cols_padded(nfields);
-    dim3 g((nfields + 31) / 32, p->T + 1);
-    if (p->prec == P_FP64)
-        k_unpack<double><<<g, 256, 0, s>>>(p->T, p->max_m, p->srow, (const double *)p->sout, Cp, nfields, p->nspec,
-                                           (double *)spec);
-    else
-        k_unpack<float><<<g, 256, 0, s>>>(p->T, p->max_m, p->srow, (const float *)p->sout, Cp, nfields, p->nspec,
-                                          (float *)spec);
-    ST_CUDA(cudaGetLastError());
-    return ST_OK;
+    PackJob J;
+    pack_job(p, 1, nfields, p->sout, spec, &J);
+    return launch_pack_jobs(1, p->prec, &J, 1, s);
 }
 
 // ---------------------------------------------------------------- export (tests)

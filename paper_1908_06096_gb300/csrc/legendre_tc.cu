@@ -29,6 +29,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <mutex>
+
 namespace st {
 
 namespace tc {
@@ -191,15 +194,11 @@ __device__ inline uint32_t idesc(int n)
            ((uint32_t)(TC_M >> 4) << 24);
 }
 
-struct Params {
-    const LegGroup *groups;
-    const LegTile *tiles;
-    long long ntiles_total;  // tiles[] entries x data tiles
-    int ncm;                 // data tiles (128 columns each)
-    const char *tab;
-    float *out;
-    int C, Cp;
-    int *err;
+template <int MAXJ>
+struct TcBatch {
+    TcJob job[MAXJ];
+    long long prefix[MAXJ + 1];  // tiles of job q: [prefix[q], prefix[q+1])
+    int njobs;
     int max_nt;
     int stages;
 };
@@ -227,14 +226,15 @@ struct Geo {
     static constexpr int A_STEP = A_MN ? UK / 8 * 1024 : 32;  // bytes per MMA K step in A
 };
 
-template <int KIND>
-__global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ CUtensorMap tmap, const Params P)
+template <int KIND, int MAXJ>
+__global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ TcBatch<MAXJ> B)
 {
     typedef Geo<KIND> G;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int S = P.stages;
-    const uint32_t b_bytes = 2u * (uint32_t)P.max_nt * 128u;
+    const int S = B.stages;
+    const uint32_t b_bytes = 2u * (uint32_t)B.max_nt * 128u;
+    const long long total = B.prefix[B.njobs];
     const uint32_t stage_bytes = 2u * G::A_PLANE + b_bytes;
     unsigned char *ctrl = smem + (size_t)S * stage_bytes;
     uint64_t *full = (uint64_t *)ctrl;
@@ -280,14 +280,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ C
             uint32_t last_par[MAX_STAGES];
             for (int s = 0; s < MAX_STAGES; ++s) last_par[s] = 0;
             bool ok = true;
-            for (long long t = blockIdx.x; ok && t < P.ntiles_total; t += gridDim.x) {
-                const LegTile lt = P.tiles[t / P.ncm];
-                const int cm = (int)(t % P.ncm);
-                const LegGroup g = P.groups[lt.g];
+            for (long long t = blockIdx.x; ok && t < total; t += gridDim.x) {
+                const int q = find_job<MAXJ>(B.prefix, B.njobs, t);
+                const TcJob &J = B.job[q];
+                const long long lt_i = t - B.prefix[q];
+                const LegTile lt = J.tiles[lt_i / J.ncm];
+                const int cm = (int)(lt_i % J.ncm);
+                const LegGroup g = J.groups[lt.g];
                 const int kc_end = (g.K + G::KC - 1) / G::KC;
                 const uint32_t bimg = 2u * (uint32_t)g.nt * 128u;
                 for (int kc = g.r0 / G::KC; kc < kc_end; ++kc) {
-                    if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, P.err, 1)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, J.err, 1)) { ok = false; break; }
                     const uint32_t fb = smem_u32(&full[stage]);
                     mbar_expect_tx(fb, 2u * G::A_PLANE + bimg);
                     const uint32_t sa = smem_base + (uint32_t)stage * stage_bytes;
@@ -297,13 +300,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ C
                         if (G::A_MN) {
 #pragma unroll
                             for (int bx = 0; bx < G::NBOX; ++bx)
-                                tma_load_3d(sa + pl * G::A_PLANE + bx * G::BOX_BYTES, &tmap, cm * TC_M + bx * G::BOX_C,
+                                tma_load_3d(sa + pl * G::A_PLANE + bx * G::BOX_BYTES, &J.map, cm * TC_M + bx * G::BOX_C,
                                             row, pl, fb);
                         } else {
-                            tma_load_3d(sa + pl * G::A_PLANE, &tmap, row, cm * TC_M, pl, fb);
+                            tma_load_3d(sa + pl * G::A_PLANE, &J.map, row, cm * TC_M, pl, fb);
                         }
                     }
-                    const char *src = P.tab + g.tab_off + (size_t)(lt.ct * g.nkc + kc) * bimg;
+                    const char *src = J.tab + g.tab_off + (size_t)(lt.ct * g.nkc + kc) * bimg;
                     bulk_load(sa + 2 * G::A_PLANE, src, bimg, fb);
                     issued_mask |= 1 << stage;
                     last_par[stage] = ph;
@@ -322,19 +325,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ C
             int local = 0;
             bool ok = true;
             bool any = false;
-            for (long long t = blockIdx.x; ok && t < P.ntiles_total; t += gridDim.x, ++local) {
-                const LegTile lt = P.tiles[t / P.ncm];
-                const LegGroup g = P.groups[lt.g];
+            for (long long t = blockIdx.x; ok && t < total; t += gridDim.x, ++local) {
+                const int q = find_job<MAXJ>(B.prefix, B.njobs, t);
+                const TcJob &J = B.job[q];
+                const LegTile lt = J.tiles[(t - B.prefix[q]) / J.ncm];
+                const LegGroup g = J.groups[lt.g];
                 const int kc_end = (g.K + G::KC - 1) / G::KC;
                 const int acc = local & 1;
                 const uint32_t acc_ph = (local >> 1) & 1;
-                if (!mbar_wait(smem_u32(&tempty[acc]), acc_ph ^ 1, abort_flag, P.err, 2)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&tempty[acc]), acc_ph ^ 1, abort_flag, J.err, 2)) { ok = false; break; }
                 fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * 256);
                 const uint32_t id = idesc<KIND>(g.nt);
                 uint32_t accum = 0;
                 for (int kc = g.r0 / G::KC; kc < kc_end; ++kc) {
-                    if (!mbar_wait(smem_u32(&full[stage]), ph, abort_flag, P.err, 2)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&full[stage]), ph, abort_flag, J.err, 2)) { ok = false; break; }
                     fence_after();
                     const uint32_t sa = smem_base + (uint32_t)stage * stage_bytes;
                     const uint32_t sb = sa + 2 * G::A_PLANE;
@@ -369,30 +374,33 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ C
         const int q = warp & 3;
         const int i = q * 32 + lane;
         int local = 0;
-        for (long long t = blockIdx.x; t < P.ntiles_total; t += gridDim.x, ++local) {
-            const LegTile lt = P.tiles[t / P.ncm];
-            const int cm = (int)(t % P.ncm);
-            const LegGroup g = P.groups[lt.g];
+        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+            const int q = find_job<MAXJ>(B.prefix, B.njobs, t);
+            const TcJob &J = B.job[q];
+            const long long lt_i = t - B.prefix[q];
+            const LegTile lt = J.tiles[lt_i / J.ncm];
+            const int cm = (int)(lt_i % J.ncm);
+            const LegGroup g = J.groups[lt.g];
             const int acc = local & 1;
             const uint32_t acc_ph = (local >> 1) & 1;
             // every lane observes the barrier; the decision to stop is warp-uniform so
             // that the .sync.aligned TMEM loads below never run in a partial warp
-            const bool ok = mbar_wait(smem_u32(&tfull[acc]), acc_ph, abort_flag, P.err, 4);
+            const bool ok = mbar_wait(smem_u32(&tfull[acc]), acc_ph, abort_flag, J.err, 4);
             if (!__all_sync(0xffffffffu, ok)) break;
             fence_after();
             const int c = cm * TC_M + i;
             const int col0 = lt.ct * g.nt;
             const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
-            float *o = P.out + g.out_row0 * (long long)P.Cp + c;
+            float *o = J.out + g.out_row0 * (long long)J.Cp + c;
             for (int j0 = 0; j0 < g.nt; j0 += 16) {
                 uint32_t r[16];
                 tmem_ld16(taddr + (uint32_t)j0, r);
                 tmem_ld_wait();
-                if (c < P.C) {
+                if (c < J.C) {
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
                         const int col = col0 + j0 + u;
-                        if (col < g.ncol) o[(long long)col * P.Cp] = __uint_as_float(r[u]);
+                        if (col < g.ncol) o[(long long)col * J.Cp] = __uint_as_float(r[u]);
                     }
                 }
             }
@@ -479,46 +487,77 @@ size_t tc_smem_bytes(int prec, int max_nt, int *stages_out)
     return 1024 + (size_t)S * stage + ctrl;
 }
 
-st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s, void *data_in, void *out_in)
+st_status tc_job(st_plan *p, int dir, int nfields, void *data, void *out, TcJob *job)
 {
+    TcJob &J = *job;
     const int C = 2 * nfields, Cp = cols_padded(nfields);
-    const int ncm = (C + TC_M - 1) / TC_M;
-    const long long total = (long long)p->ntiles[dir] * ncm;
-    if (total == 0) return ST_OK;
     const bool bf16 = p->prec == P_BF16X3;
-    void *data = data_in ? data_in : (dir == 0 ? p->sop : p->fbop);
-    void *out = out_in ? out_in : (dir == 0 ? p->fb : p->sout);
     const long long rows = dir == 0 ? p->srow_total : fb_rows(p);
-    CUtensorMap map;
-    st_status r = make_operand_map(&map, data, bf16, C, rows, Cp);
+    st_status r = make_operand_map(&J.map, data, bf16, C, rows, Cp);
     if (r != ST_OK) return r;
-    tc::Params P;
-    P.groups = p->groups[dir];
-    P.tiles = p->tiles[dir];
-    P.ntiles_total = total;
-    P.ncm = ncm;
-    P.tab = (const char *)p->tab[dir];
-    P.out = (float *)out;
-    P.C = C;
-    P.Cp = Cp;
-    P.err = p->err;
-    P.max_nt = tc_max_nt(p, dir);
+    J.groups = p->groups[dir];
+    J.tiles = p->tiles[dir];
+    J.tab = (const char *)p->tab[dir];
+    J.out = (float *)out;
+    J.err = p->err;
+    J.C = C;
+    J.Cp = Cp;
+    J.ncm = (C + TC_M - 1) / TC_M;
+    J.ntiles = (long long)p->ntiles[dir] * J.ncm;
+    J.max_nt = tc_max_nt(p, dir);
+    return ST_OK;
+}
+
+template <int MAXJ>
+static st_status run_tc_batch(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s)
+{
+    tc::TcBatch<MAXJ> B;  // copied into the kernel's parameters at launch
+    B.njobs = n;
+    long long tot = 0;
+    int max_nt = 16;
+    for (int q = 0; q < n; ++q) {
+        B.prefix[q] = tot;
+        B.job[q] = jobs[q];
+        tot += jobs[q].ntiles;
+        max_nt = std::max(max_nt, jobs[q].max_nt);
+    }
+    B.prefix[n] = tot;
+    if (tot == 0) return ST_OK;
+    B.max_nt = max_nt;
     int S = 0;
-    const size_t smem = tc_smem_bytes(p->prec, P.max_nt, &S);
+    const size_t smem = tc_smem_bytes(prec, max_nt, &S);
     if (S < 2) return ST_ERR_UNSUPPORTED;
-    P.stages = S;
-    const int grid = (int)(total < p->sm_count ? total : p->sm_count);
-    if (bf16) {
-        auto k = tc::k_leg_tc<0>;
+    B.stages = S;
+    const int grid = (int)(tot < sm_count ? tot : sm_count);
+    if (prec == P_BF16X3) {
+        auto k = tc::k_leg_tc<0, MAXJ>;
         ST_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, tc::THREADS, smem, s>>>(map, P);
+        k<<<grid, tc::THREADS, smem, s>>>(B);
     } else {
-        auto k = tc::k_leg_tc<1>;
+        auto k = tc::k_leg_tc<1, MAXJ>;
         ST_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<grid, tc::THREADS, smem, s>>>(map, P);
+        k<<<grid, tc::THREADS, smem, s>>>(B);
     }
     ST_CUDA(cudaGetLastError());
     return ST_OK;
+}
+
+st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s)
+{
+    if (n <= 0) return ST_OK;
+    if (n > MAX_JOBS) return ST_ERR_ARG;
+    if (n == 1) return run_tc_batch<1>(prec, jobs, n, sm_count, s);
+    return run_tc_batch<MAX_JOBS>(prec, jobs, n, sm_count, s);
+}
+
+st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s, void *data_in, void *out_in)
+{
+    void *data = data_in ? data_in : (dir == 0 ? p->sop : p->fbop);
+    void *out = out_in ? out_in : (dir == 0 ? p->fb : p->sout);
+    TcJob J;
+    st_status r = tc_job(p, dir, nfields, data, out, &J);
+    if (r) return r;
+    return launch_tc_jobs(p->prec, &J, 1, p->sm_count, s);
 }
 
 }  // namespace st

@@ -2,6 +2,7 @@
 // spherical-harmonic transform library.  Nothing here is part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -123,6 +124,69 @@ struct LegTile {
     int ct;                   // column tile
 };
 
+// ---- batched launches: every kernel takes up to MAX_JOBS per-request jobs in
+// its launch parameters; a CTA (or a persistent tile) finds its job by binary
+// search over the jobs' prefix sums.  A single-plan call is a batch of one.
+constexpr int MAX_JOBS = 64;
+
+template <int MAXJ>
+__device__ inline int find_job(const long long *prefix, int njobs, long long b)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One FFT stage of one request.
+struct FftJob {
+    const RowPair *rps;
+    const void *tw, *chirp, *kern;
+    const void *src;          // direct: grid; inverse: Fourier buffer (S, A)
+    void *dst;                // direct: Fourier-buffer operand (E, O); inverse: grid
+    long long npts, Rp, ps;
+    int nfields, G, Sslot, Cp, T, Jp, J, nfg;
+};
+template <int MAXJ>
+struct FftBatch {
+    int njobs;
+    long long prefix[MAXJ + 1];  // CTAs of job q: [prefix[q], prefix[q+1])
+    FftJob job[MAXJ];
+};
+
+// Spectral pack (inverse) or unpack (direct) of one request.
+struct PackJob {
+    const void *src;
+    void *dst;
+    const long long *srow;
+    long long nspec, Rp, ps;
+    int T, max_m, nfields, Cp, nft, nm;  // nft field tiles of 32, nm wavenumbers launched
+};
+template <int MAXJ>
+struct PackBatch {
+    int njobs;
+    long long prefix[MAXJ + 1];
+    PackJob job[MAXJ];
+};
+
+// SIMT Legendre stage of one request.
+struct SimtJob {
+    const LegGroup *groups;
+    const LegTile *tiles;
+    const void *tab, *data;
+    void *out;
+    int ncm, C, Cp;
+};
+template <int MAXJ>
+struct SimtBatch {
+    int njobs;
+    long long prefix[MAXJ + 1];
+    SimtJob job[MAXJ];
+};
+
 }  // namespace st
 
 // The plan object behind st_plan_t.
@@ -218,6 +282,28 @@ enum KernelKind {
     K_PACK = 0, K_LEG_INV, K_FFT_INV, K_FFT_DIR, K_LEG_DIR, K_UNPACK, K_EXPORT, K_TABLES, K_NKINDS
 };
 const char *kernel_name(const st_plan *p, int kind);
+
+// ---- job builders and batched launchers ----
+st_status fft_job(st_plan *p, int dir, int nfields, const void *src, void *dst, FftJob *job, size_t *smem);
+st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s);
+st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job);
+st_status launch_pack_jobs(int dir, int prec, const PackJob *jobs, int n, cudaStream_t s);
+st_status simt_job(st_plan *p, int dir, int nfields, const void *data, void *out, SimtJob *job, long long *blocks);
+st_status launch_simt_jobs(int prec, const SimtJob *jobs, const long long *blocks, int n, cudaStream_t s);
+// Tensor-core Legendre stage of one request (the data operand's tensor map
+// travels with it).
+struct TcJob {
+    CUtensorMap map;
+    const LegGroup *groups;
+    const LegTile *tiles;
+    const char *tab;
+    float *out;
+    int *err;
+    long long ntiles;         // tiles[] entries x data tiles
+    int ncm, C, Cp, max_nt;
+};
+st_status tc_job(st_plan *p, int dir, int nfields, void *data, void *out, TcJob *job);
+st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s);
 
 // ---- launchers implemented in the .cu files ----
 st_status launch_tables(st_plan *p, cudaStream_t s);

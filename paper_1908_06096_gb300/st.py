@@ -40,6 +40,11 @@ class _PlanInfo(ctypes.Structure):
                 ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("direction", ctypes.c_int), ("spec_in", ctypes.c_void_p),
+                ("grid", ctypes.c_void_p), ("spec_out", ctypes.c_void_p), ("nfields", ctypes.c_int)]
+
+
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double),
                 ("timed", ctypes.c_longlong)]
@@ -72,6 +77,9 @@ SIGNATURES = {
     "st_plan_timings": [_VP, ctypes.POINTER(_KernelTime), _I, ctypes.POINTER(ctypes.c_int)],
     "st_plan_reset_timings": [_VP],
     "st_inv_trans_static": [_VP, _VP, _VP, _I, _VP],
+    "st_batch_create": [ctypes.POINTER(_VP), ctypes.POINTER(_BatchItem), _I],
+    "st_batch_run": [_VP, _VP, _I],
+    "st_batch_destroy": [_VP],
     "st_static_scratch_bytes": [],
 }
 
@@ -270,3 +278,42 @@ class Plan:
         _check(load().st_fourier_export(self._h, direction, nf, _ptr(out), _stream_handle(stream)),
                "st_fourier_export")
         return torch.view_as_complex(out)
+
+
+class Batch:
+    """Many transforms in one set of launches (st_batch_*).
+
+    items: list of (plan, direction, spec_in, grid, spec_out) with direction
+    "inv", "dir" or "round" and torch tensors (None where unused).  The
+    tensors must stay alive as long as the batch.
+    """
+
+    DIRS = {"inv": 0, "dir": 1, "round": 2}
+
+    def __init__(self, items):
+        lib = load()
+        arr = (_BatchItem * len(items))()
+        self._keep = []
+        for i, (plan, direction, spec_in, grid, spec_out) in enumerate(items):
+            nf = grid.numel() // plan.npts
+            arr[i] = _BatchItem(plan.handle.value, self.DIRS[direction],
+                                spec_in.data_ptr() if spec_in is not None else None, grid.data_ptr(),
+                                spec_out.data_ptr() if spec_out is not None else None, nf)
+            self._keep.append((plan, spec_in, grid, spec_out))
+        h = _VP()
+        _check(lib.st_batch_create(ctypes.byref(h), arr, len(items)), "st_batch_create")
+        self._h = h
+
+    def run(self, stream=None, graph: bool = True):
+        _check(load().st_batch_run(self._h, _stream_handle(stream), 1 if graph else 0), "st_batch_run")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().st_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
