@@ -109,6 +109,17 @@ typedef struct {
 st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int prec,
                          int max_fields, void *stream);
 
+/*
+ * A second plan with the same transform as `base` that shares base's
+ * read-only device data (Gaussian nodes, Legendre tables, FFT row data) and
+ * owns only a new workspace for up to max_fields fields.  Plans sharing data
+ * can run concurrently on different streams (each has its own workspace);
+ * the shared data is freed with the last plan that holds it, in any order.
+ * Not in the paper: it lets a server keep one set of tables per truncation
+ * resident while several requests of that truncation are in flight.
+ */
+st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, void *stream);
+
 /* Release everything the plan holds.  NULL is accepted.  The caller must make
  * sure no work on the plan is still in flight. */
 st_status st_plan_destroy(st_plan_t plan);

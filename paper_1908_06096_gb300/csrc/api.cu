@@ -148,13 +148,30 @@ static st_status dmalloc(st_plan *p, T **ptr, size_t bytes)
     return ST_OK;
 }
 
+// Owner of a plan's read-only device arrays (shared between plans).
+struct TableCore {
+    std::vector<void *> ptrs;
+    ~TableCore()
+    {
+        for (void *q : ptrs)
+            if (q) cudaFree(q);
+    }
+};
+
 static void plan_free(st_plan *p)
 {
     if (!p) return;
-    void *ptrs[] = {p->mu, p->w, p->rowpairs, p->tw, p->chirp, p->kern, p->tab[0], p->tab[1], p->groups[0],
-                    p->groups[1], p->tiles[0], p->tiles[1], p->fb, p->fbop, p->sop, p->sout, p->err, p->srow};
-    for (void *q : ptrs)
+    void *ws[] = {p->fb, p->fbop, p->sop, p->sout, p->err};
+    for (void *q : ws)
         if (q) cudaFree(q);
+    if (!p->core) {
+        // creation failed before the read-only arrays were handed to a core
+        void *ro[] = {p->mu, p->w, p->rowpairs, p->tw, p->chirp, p->kern, p->tab[0], p->tab[1], p->groups[0],
+                      p->groups[1], p->tiles[0], p->tiles[1], p->srow};
+        for (void *q : ro)
+            if (q) cudaFree(q);
+    }
+    p->core.reset();
     for (auto &e : p->pending) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -251,6 +268,32 @@ static std::vector<LegTile> build_tiles(const st_plan *p, int dir)
     return out;
 }
 
+// Per-plan workspace for up to max_fields fields, and the error word.  GEMM
+// data operands live in buffers of their own, zeroed once here (see st_plan).
+static st_status alloc_workspace(st_plan *p, cudaStream_t s)
+{
+    st_status r;
+    if ((r = dmalloc(p, &p->err, sizeof(int)))) return r;
+    ST_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+    const int Cp = cols_padded(p->max_fields);
+    const int sb = store_bytes(store_of(p->prec)) * store_planes(store_of(p->prec));
+    const int ob = p->prec == P_FP64 ? 8 : 4;
+    p->fb_bytes = (size_t)fb_rows(p) * Cp * ob;
+    p->fbop_bytes = (size_t)fb_rows(p) * Cp * sb;
+    p->sop_bytes = (size_t)p->srow_total * Cp * sb;
+    p->sout_bytes = (size_t)p->srow_total * Cp * ob;
+    if ((r = dmalloc(p, &p->fb, p->fb_bytes))) return r;
+    if ((r = dmalloc(p, &p->fbop, p->fbop_bytes))) return r;
+    if ((r = dmalloc(p, &p->sop, p->sop_bytes))) return r;
+    if ((r = dmalloc(p, &p->sout, p->sout_bytes))) return r;
+    ST_CUDA(cudaMemsetAsync(p->fb, 0, p->fb_bytes, s));
+    ST_CUDA(cudaMemsetAsync(p->fbop, 0, p->fbop_bytes, s));
+    ST_CUDA(cudaMemsetAsync(p->sop, 0, p->sop_bytes, s));
+    ST_CUDA(cudaMemsetAsync(p->sout, 0, p->sout_bytes, s));
+    p->workspace_bytes = p->fb_bytes + p->fbop_bytes + p->sop_bytes + p->sout_bytes;
+    return ST_OK;
+}
+
 static st_status plan_build(st_plan *p, cudaStream_t s)
 {
     const int T = p->T, nlat = p->nlat, J = nlat / 2;
@@ -290,8 +333,6 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
             if (p->Mrow[j] >= m) { p->j0[m] = j; break; }
 
     st_status r;
-    if ((r = dmalloc(p, &p->err, sizeof(int)))) return r;
-    ST_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), s));
 
     // nodes and weights
     if ((r = dmalloc(p, &p->mu, sizeof(double) * nlat))) return r;
@@ -381,23 +422,14 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     }
     if ((r = launch_tables(p, s))) return r;
 
-    // workspace
-    const int Cp = cols_padded(p->max_fields);
-    const int sb = store_bytes(store_of(p->prec)) * store_planes(store_of(p->prec));
-    const int ob = p->prec == P_FP64 ? 8 : 4;
-    p->fb_bytes = (size_t)fb_rows(p) * Cp * ob;
-    p->fbop_bytes = (size_t)fb_rows(p) * Cp * sb;
-    p->sop_bytes = (size_t)p->srow_total * Cp * sb;
-    p->sout_bytes = (size_t)p->srow_total * Cp * ob;
-    if ((r = dmalloc(p, &p->fb, p->fb_bytes))) return r;
-    if ((r = dmalloc(p, &p->fbop, p->fbop_bytes))) return r;
-    if ((r = dmalloc(p, &p->sop, p->sop_bytes))) return r;
-    if ((r = dmalloc(p, &p->sout, p->sout_bytes))) return r;
-    ST_CUDA(cudaMemsetAsync(p->fb, 0, p->fb_bytes, s));
-    ST_CUDA(cudaMemsetAsync(p->fbop, 0, p->fbop_bytes, s));
-    ST_CUDA(cudaMemsetAsync(p->sop, 0, p->sop_bytes, s));
-    ST_CUDA(cudaMemsetAsync(p->sout, 0, p->sout_bytes, s));
-    p->workspace_bytes = p->fb_bytes + p->fbop_bytes + p->sop_bytes + p->sout_bytes;
+    // the read-only arrays now belong to a shareable core
+    {
+        auto core = std::make_shared<TableCore>();
+        core->ptrs = {p->mu, p->w, p->rowpairs, p->tw, p->chirp, p->kern, p->tab[0], p->tab[1], p->groups[0],
+                      p->groups[1], p->tiles[0], p->tiles[1], p->srow};
+        p->core = core;
+    }
+    if ((r = alloc_workspace(p, s))) return r;
 
     if (prec_is_tc(p->prec)) {
         for (int dir = 0; dir < 2; ++dir) {
@@ -552,6 +584,46 @@ st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int pr
     st_status r = plan_build(p, s);
     if (r != ST_OK) {
         cudaStreamSynchronize(s);
+        plan_free(p);
+        return r;
+    }
+    *out = p;
+    return ST_OK;
+}
+
+st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, void *stream)
+{
+    if (!out) return ST_ERR_ARG;
+    *out = nullptr;
+    if (!base || !base->core || max_fields < 1) return ST_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    st_plan *p = new st_plan();
+    // host metadata and read-only device pointers as in the base plan
+    p->T = base->T; p->nlat = base->nlat; p->J = base->J; p->Jp = base->Jp; p->kind = base->kind;
+    p->nlon = base->nlon; p->prec = base->prec; p->max_m = base->max_m; p->device = base->device;
+    p->sm_count = base->sm_count; p->rows = base->rows; p->Mrow = base->Mrow; p->j0 = base->j0;
+    p->npts = base->npts; p->nspec = base->nspec; p->srow_h = base->srow_h; p->srow = base->srow;
+    p->srow_total = base->srow_total; p->mu = base->mu; p->w = base->w; p->rowpairs = base->rowpairs;
+    p->rowpairs_h = base->rowpairs_h; p->tw = base->tw; p->ntw = base->ntw; p->chirp = base->chirp;
+    p->kern = base->kern; p->nchirp = base->nchirp; p->nkern = base->nkern; p->max_row = base->max_row;
+    p->max_fft = base->max_fft; p->max_chirp = base->max_chirp; p->max_fft_smem = base->max_fft_smem;
+    for (int d = 0; d < 2; ++d) {
+        p->tab[d] = base->tab[d];
+        p->tab_bytes[d] = base->tab_bytes[d];
+        p->groups[d] = base->groups[d];
+        p->groups_h[d] = base->groups_h[d];
+        p->tiles[d] = base->tiles[d];
+        p->ntiles[d] = base->ntiles[d];
+    }
+    p->table_bytes = base->table_bytes;
+    p->core = base->core;
+    p->max_fields = max_fields;
+    st_status r = alloc_workspace(p, s);
+    if (r == ST_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) r = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (r != ST_OK) {
         plan_free(p);
         return r;
     }

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -241,6 +242,11 @@ struct st_plan {
     int *err = nullptr;       // device error word (bit flags set by bounded waits)
 
     size_t device_bytes = 0, table_bytes = 0, workspace_bytes = 0;
+
+    // Read-only device data (nodes, FFT rows, tables, groups, tiles, row
+    // bases) may be shared by several plans (st_plan_create_shared); it is
+    // freed when the last plan holding it is destroyed.
+    std::shared_ptr<void> core;
 
     // launch accounting and optional event timing, per kernel kind
     bool timing = false;

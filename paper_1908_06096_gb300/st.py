@@ -58,6 +58,7 @@ _VP, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "st_plan_create": [ctypes.POINTER(_VP), _I, ctypes.POINTER(_GridDesc), _I, _I, _VP],
     "st_plan_destroy": [_VP],
+    "st_plan_create_shared": [ctypes.POINTER(_VP), _VP, _I, _VP],
     "st_plan_query": [_VP, ctypes.POINTER(_PlanInfo)],
     "st_plan_row_lengths": [_VP, ctypes.POINTER(ctypes.c_int)],
     "st_plan_nodes": [_VP, _D, _D],
@@ -152,8 +153,23 @@ class Plan:
     """
 
     def __init__(self, T: int, grid: str = "regular", nlat: int | None = None, nlon: int | None = None,
-                 precision: str = "bf16x3", max_fields: int = 1, stream=None):
+                 precision: str = "bf16x3", max_fields: int = 1, stream=None, share_with: "Plan | None" = None):
         lib = load()
+        if share_with is not None:
+            src = share_with
+            self.T, self.grid, self.nlat, self.nlon = src.T, src.grid, src.nlat, src.nlon
+            self.precision, self.prec_code, self.max_fields = src.precision, src.prec_code, max_fields
+            h = _VP()
+            _check(lib.st_plan_create_shared(ctypes.byref(h), src.handle, max_fields, _stream_handle(stream)),
+                   "st_plan_create_shared")
+            self._h = h
+            info = _PlanInfo()
+            _check(lib.st_plan_query(h, ctypes.byref(info)), "st_plan_query")
+            self.info = info
+            self.nspec = int(info.spec_elems)
+            self.npts = int(info.grid_points)
+            self.dtype = src.dtype
+            return
         if nlat is None:
             nlat = T + 1 if grid == "regular" else 2 * (T + 1)
             nlat += nlat & 1
