@@ -387,6 +387,17 @@ def run_ours(args, ws, rank, local):
         forms[prec] = {"value": value, "ms_per_step": ms, "steps": args.steps}
         out["forms"] = forms
 
+    plan.close()
+    del spec, g, s_out
+    torch.cuda.empty_cache()
+    if not args.skip_batch:
+        out["batch_mixed"] = mixed_batch(args, dev)
+    if not args.skip_serving:
+        sv = serving(args, dev)
+        out["serving"] = sv
+        out["latency_ms"] = {"p50": sv["rates"]["0.7"]["p50_ms"], "p99": sv["rates"]["0.7"]["p99_ms"],
+                             "at": "0.7 x saturated request rate"}
+
     if not args.no_cpu_baseline and rank == 0 and ws == 1:
         try:
             out["cpu_baseline"] = cpu_baseline(wl, args.cpu_fields)
@@ -394,7 +405,91 @@ def run_ours(args, ws, rank, local):
             out["cpu_baseline"] = {"error": repr(ex)}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    plan.close()
+
+
+def mixed_batch(args, dev):
+    """The 48-request mixed batch: T uniform over {79,159,255,319,511,639},
+    regular (T+1) x (2T+2) or octahedral O(T+1) grids, 1-256 fields each,
+    BF16x3; one round trip per request, all requests in one batch (one launch
+    per stage, replayed from a CUDA graph)."""
+    import torch
+
+    from paper_1908_06096_gb300 import inputs, st
+    reqs = inputs.mixed_requests(48, seed=1003)
+    plans, items, keep = [], [], []
+    fields = 0
+    for r in reqs:
+        p = st.Plan(r["T"], r["grid"], precision="bf16x3", max_fields=r["nfields"])
+        spec = torch.from_numpy(inputs.spectra(r["T"], r["nfields"], seed=r["seed"])).to(dev, p.dtype)
+        g = torch.empty((r["nfields"], p.npts), dtype=p.dtype, device=dev)
+        out = torch.empty_like(spec)
+        plans.append(p)
+        items.append((p, "round", spec, g, out))
+        fields += r["nfields"]
+    batch = st.Batch(items)
+    for _ in range(max(3, args.warmup)):
+        batch.run(graph=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(3, args.steps)
+    e0.record()
+    for _ in range(n):
+        batch.run(graph=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    # the same requests one plan call after another, for comparison
+    e0.record()
+    for p, _, spec, g, out in items:
+        p.inv(spec, out=g)
+        p.dir(g, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    batch.close()
+    for p in plans:
+        p.close()
+    del items, plans, batch
+    torch.cuda.empty_cache()
+    return {"requests": len(reqs), "fields": fields, "ms_per_batch": ms,
+            "field_transforms_per_s": fields / (ms * 1e-3),
+            "ms_one_call_per_request": ms_seq,
+            "mix": "T uniform over {79,159,255,319,511,639}, regular or octahedral, 1-256 fields, seed 1003",
+            "precision": "bf16x3", "launch": "one batch: one launch per stage for all requests, CUDA-graph replay"}
+
+
+def serving(args, dev):
+    """Serving: T uniform over {63,127,255,511,1279} on regular grids, 1-137
+    fields, inverse or direct with equal odds, Poisson arrivals; BF16x3, tables
+    resident, 4 slots, 32 GB admission budget.  Saturated rate first, then
+    arrivals at 0.5 / 0.7 / 0.9 of it."""
+    import torch
+
+    from paper_1908_06096_gb300 import inputs, serve
+    srv = serve.Server(inputs.SERVE_T, precision="bf16x3", slots=4, max_fields=137, budget_bytes=32 << 30)
+    payloads = {}
+    for T, p in srv.base.items():
+        payloads[(T, "inv")] = torch.from_numpy(inputs.spectra(T, 137, seed=T)).to(torch.float32).pin_memory()
+        payloads[(T, "dir")] = torch.randn((137, p.npts), generator=torch.Generator().manual_seed(T)).pin_memory()
+    n = args.serve_requests
+    specs = inputs.serve_requests(max(n, 1), seed=1004, rate_hz=1e12)       # all at t = 0
+    srv.run(serve.make_requests(specs[:min(200, n)], payloads))              # warm-up
+    sat = srv.run(serve.make_requests(specs, payloads))
+    rate_sat = sat["requests_per_s"]
+    out = {"saturated": sat, "rates": {}}
+    for frac in (0.5, 0.7, 0.9):
+        # at most ~20 s of arrivals per rate
+        nr = max(200, min(n, int(frac * rate_sat * 20)))
+        sp = inputs.serve_requests(nr, seed=1004, rate_hz=frac * rate_sat)
+        out["rates"][str(frac)] = srv.run(serve.make_requests(sp, payloads))
+        out["rates"][str(frac)]["rate_hz"] = frac * rate_sat
+    out["mix"] = ("T uniform over {63,127,255,511,1279} regular grids, 1-137 fields, inverse or direct 50/50, "
+                  f"Poisson arrivals, up to {n} requests per rate, seed 1004")
+    out["server"] = {"slots": 4, "max_fields_per_call": 137, "budget_bytes": 32 << 30,
+                     "resident_bytes": srv.resident_bytes}
+    srv.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def per_field(x, ref):
@@ -429,6 +524,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-fields", type=int, default=8)
     ap.add_argument("--ref-fields", type=int, default=2)
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -122,8 +122,9 @@ class Server:
         slot.event = ev
         slot.kind = (T, direction, per_out)
 
-    def _complete(self, slot: _Slot, t0_event: torch.cuda.Event, t0: float):
-        t_done = t0 + t0_event.elapsed_time(slot.event) * 1e-3
+    def _complete(self, slot: _Slot, t0_event: torch.cuda.Event):
+        # seconds from the start of the run, on the device clock
+        t_done = t0_event.elapsed_time(slot.event) * 1e-3
         T, direction, per_out = slot.kind
         off = 0
         for r in slot.busy:
@@ -137,9 +138,13 @@ class Server:
         return done
 
     def run(self, requests: list) -> dict:
-        """Serve `requests` (sorted by t_arrival); returns latency statistics."""
+        """Serve `requests` (any order; arrivals from t_arrival); returns
+        latency statistics.  Waiting requests are queued per (T, direction);
+        a free slot takes the oldest waiting request and the following ones of
+        its queue that fit."""
         pending = collections.deque(sorted(requests, key=lambda r: r.t_arrival))
-        waiting: list = []
+        queues: dict = collections.OrderedDict()
+        nwait = 0
         inflight_bytes = 0
         finished = []
         t0_event = torch.cuda.Event(enable_timing=True)
@@ -148,40 +153,44 @@ class Server:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         foot = {}
-        while pending or waiting or any(s.busy for s in self.slots):
+        peak_inflight = 0
+        while pending or nwait or any(s.busy for s in self.slots):
             now = time.perf_counter() - t0
             while pending and pending[0].t_arrival <= now:
-                waiting.append(pending.popleft())
+                r = pending.popleft()
+                queues.setdefault((r.T, r.direction), collections.deque()).append(r)
+                nwait += 1
             for s in self.slots:
                 if s.busy and s.event.query():
-                    for r in self._complete(s, t0_event, t0):
+                    for r in self._complete(s, t0_event):
                         inflight_bytes -= foot.pop(r.rid)
                         finished.append(r)
             for s in self.slots:
-                if s.busy or not waiting:
+                if s.busy or not nwait:
                     continue
-                head = waiting[0]
+                key = min((k for k, q in queues.items() if q), key=lambda k: queues[k][0].t_arrival)
+                q = queues[key]
+                head = q[0]
                 fh = self.footprint(head)
                 if inflight_bytes + fh > self.budget and inflight_bytes > 0:
                     break  # admission by footprint: wait for memory to free up
                 # (a request larger than the whole budget runs alone)
-                batch, nf, fb = [head], head.nfields, fh
-                for r in waiting[1:]:
-                    if r.T != head.T or r.direction != head.direction:
-                        continue
+                batch, nf, fb = [q.popleft()], head.nfields, fh
+                while q:
+                    r = q[0]
                     f = self.footprint(r)
                     if nf + r.nfields > self.max_fields or inflight_bytes + fb + f > self.budget:
-                        continue
-                    batch.append(r)
+                        break
+                    batch.append(q.popleft())
                     nf += r.nfields
                     fb += f
-                ids = {r.rid for r in batch}
-                waiting = [r for r in waiting if r.rid not in ids]
+                nwait -= len(batch)
                 for r in batch:
                     foot[r.rid] = self.footprint(r)
                 inflight_bytes += fb
+                peak_inflight = max(peak_inflight, inflight_bytes)
                 self._launch(s, batch, t0_event)
-            if not waiting and pending and not any(s.busy for s in self.slots):
+            if not nwait and pending and not any(s.busy for s in self.slots):
                 dt = pending[0].t_arrival - (time.perf_counter() - t0)
                 if dt > 2e-4:
                     time.sleep(dt - 1e-4)
@@ -192,7 +201,8 @@ class Server:
         return {"requests": len(finished), "fields": fields, "wall_s": wall,
                 "field_transforms_per_s": fields / wall, "requests_per_s": len(finished) / wall,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3)}
+                "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
+                "peak_inflight_bytes": int(peak_inflight)}
 
 
 def make_requests(specs, payloads) -> list:

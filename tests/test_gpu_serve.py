@@ -74,4 +74,7 @@ def test_admission_never_exceeds_budget(st_mod):
     stats = srv.run(reqs)
     assert stats["requests"] == 12
     assert 0 < peak["v"] <= srv.budget
+    assert 0 < stats["peak_inflight_bytes"] <= srv.budget
+    # latencies are measured from arrival on the run's own clock
+    assert 0 < stats["p50_ms"] <= stats["max_ms"] < 60_000
     srv.close()
