@@ -121,7 +121,8 @@ def geometry(rows, T):
 
 def algorithmic(T, rows, F, prec):
     """Algorithmic work of one launch of each kernel for F fields (the counts
-    the roofline fractions divide by; see DESIGN.md)."""
+    the roofline fractions divide by)."""
+    rows = [int(r) for r in rows]
     J, M, max_m, j0 = geometry(rows, T)
     npts = sum(rows)
     nspec = (T + 1) * (T + 2) // 2
@@ -501,13 +502,24 @@ def per_field(x, ref):
 
 
 def load_traffic(kernel, wl, prec):
-    """dram read+write bytes per launch from the committed ncu summary of this
-    kernel (null if none matches the current build)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """dram read+write bytes per launch of `kernel` from the committed ncu
+    summary (profiles/traffic.txt), or None when there is none for this
+    workload or it was taken on other kernel sources than the current ones."""
+    from paper_1908_06096_gb300 import build
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
+        fp, vals = None, {}
         with open(path) as fh:
-            d = json.load(fh)
-        return d.get(f"{kernel}|{wl}|{prec}")
+            for line in fh:
+                line = line.strip()
+                if line.startswith("# source fingerprint:"):
+                    fp = line.split(":", 1)[1].strip()
+                elif line and not line.startswith("#"):
+                    k, w, pr, v = line.split()[:4]
+                    vals[(k, w, pr)] = float(v)
+        if fp != build.source_fingerprint():
+            return None
+        return vals.get((kernel, wl, prec))
     except Exception:
         return None
 

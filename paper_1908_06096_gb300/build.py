@@ -45,6 +45,20 @@ def _fingerprint() -> str:
     return h.hexdigest()
 
 
+def source_fingerprint() -> str:
+    """Hash of the CUDA sources and headers only (host-independent): a
+    profile summary records it so that counters taken on an older build are
+    recognised as stale."""
+    h = hashlib.sha256()
+    files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
+        sorted(glob.glob(os.path.join(INCLUDE, "*.h")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     stamp = LIB + ".stamp"
     if not (os.path.exists(LIB) and os.path.exists(stamp)):
