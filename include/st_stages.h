@@ -53,6 +53,17 @@ st_status st_dir_legendre(st_plan_t plan, void *spec_dev, int nfields, void *str
 st_status st_fourier_export(st_plan_t plan, int direction, int nfields, double *out_dev,
                             void *stream);
 
+/*
+ * Failure-path test hook (not in the paper).  what = 1: the plan's next
+ * tensor-core Legendre launch issues no operand copies, so the bounded wait
+ * of its MMA issuer on the first stage runs out after wait_ms milliseconds;
+ * the kernel then records the timeout, stops its other roles, frees its
+ * tensor memory and returns, and the next st_plan_sync reports
+ * ST_ERR_TIMEOUT.  Nothing faults, traps or hangs, and the plan stays usable.
+ * what = 0 clears a pending injection.  ST_ERR_UNSUPPORTED for SIMT plans.
+ */
+st_status st_plan_inject(st_plan_t plan, int what, unsigned wait_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -765,6 +765,15 @@ st_status st_fourier_export(st_plan_t p, int direction, int nfields, double *out
     return counted(p, K_EXPORT, s, [&] { return launch_fourier_export(p, direction, nfields, out_dev, s); });
 }
 
+st_status st_plan_inject(st_plan_t p, int what, unsigned wait_ms)
+{
+    if (!p || what < 0 || what > 1 || (what == 1 && (wait_ms < 1 || wait_ms > 2000))) return ST_ERR_ARG;
+    if (!prec_is_tc(p->prec)) return ST_ERR_UNSUPPORTED;
+    p->inject_withhold = what;
+    p->inject_wait_ns = (unsigned long long)wait_ms * 1000000ull;
+    return ST_OK;
+}
+
 st_status st_plan_set_timing(st_plan_t p, int enable)
 {
     if (!p) return ST_ERR_ARG;

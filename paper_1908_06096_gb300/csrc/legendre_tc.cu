@@ -80,14 +80,15 @@ __device__ inline bool mbar_try_wait(uint32_t bar, uint32_t parity)
 // Bounded wait for the phase of parity `parity` to complete.  Returns false
 // if the CTA is aborting or the wait ran past WAIT_NS (then it starts the
 // abort and records `code` in the error word).
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code)
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err, int code,
+                                 uint64_t wait_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     uint64_t t0 = gtimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (gtimer() - t0 > WAIT_NS) {
+        if (gtimer() - t0 > wait_ns) {
             *abort_flag = 1;
             atomicOr(err, code);
             return false;
@@ -96,11 +97,11 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *ab
 }
 
 // Drain wait (used after an abort): bounded, records nothing.
-__device__ inline void mbar_drain(uint32_t bar, uint32_t parity)
+__device__ inline void mbar_drain(uint32_t bar, uint32_t parity, uint64_t wait_ns)
 {
     uint64_t t0 = gtimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (gtimer() - t0 > WAIT_NS) return;
+        if (gtimer() - t0 > wait_ns) return;
     }
 }
 
@@ -201,6 +202,8 @@ struct TcBatch {
     int njobs;
     int max_nt;
     int stages;
+    int withhold_loads;          // fault injection (tests): the producer issues no copies
+    unsigned long long wait_ns;  // bound of every wait in this launch
 };
 
 // BF16 (KIND 0): the data operand A is MN-major (data columns contiguous in
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ T
     const int S = B.stages;
     const uint32_t b_bytes = 2u * (uint32_t)B.max_nt * 128u;
     const long long total = B.prefix[B.njobs];
+    const uint64_t wait_ns = B.wait_ns;
     const uint32_t stage_bytes = 2u * G::A_PLANE + b_bytes;
     unsigned char *ctrl = smem + (size_t)S * stage_bytes;
     uint64_t *full = (uint64_t *)ctrl;
@@ -290,8 +294,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ T
                 const int kc_end = (g.K + G::KC - 1) / G::KC;
                 const uint32_t bimg = 2u * (uint32_t)g.nt * 128u;
                 for (int kc = g.r0 / G::KC; kc < kc_end; ++kc) {
-                    if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, J.err, 1)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&empty[stage]), ph ^ 1, abort_flag, J.err, 1, wait_ns)) { ok = false; break; }
                     const uint32_t fb = smem_u32(&full[stage]);
+                    if (B.withhold_loads) {
+                        // injected fault: nothing arms this stage, so the MMA issuer's
+                        // bounded wait on it runs out
+                        if (++stage == S) { stage = 0; ph ^= 1; }
+                        continue;
+                    }
                     mbar_expect_tx(fb, 2u * G::A_PLANE + bimg);
                     const uint32_t sa = smem_base + (uint32_t)stage * stage_bytes;
                     const int row = (int)(g.data_row0 + (long long)kc * G::KC);
@@ -315,7 +325,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ T
             }
             // make sure no copy into this CTA's shared memory is still in flight
             for (int s = 0; s < S; ++s)
-                if (issued_mask & (1 << s)) mbar_drain(smem_u32(&full[s]), last_par[s]);
+                if (issued_mask & (1 << s)) mbar_drain(smem_u32(&full[s]), last_par[s], wait_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -333,13 +343,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ T
                 const int kc_end = (g.K + G::KC - 1) / G::KC;
                 const int acc = local & 1;
                 const uint32_t acc_ph = (local >> 1) & 1;
-                if (!mbar_wait(smem_u32(&tempty[acc]), acc_ph ^ 1, abort_flag, J.err, 2)) { ok = false; break; }
+                if (!mbar_wait(smem_u32(&tempty[acc]), acc_ph ^ 1, abort_flag, J.err, 2, wait_ns)) { ok = false; break; }
                 fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * 256);
                 const uint32_t id = idesc<KIND>(g.nt);
                 uint32_t accum = 0;
                 for (int kc = g.r0 / G::KC; kc < kc_end; ++kc) {
-                    if (!mbar_wait(smem_u32(&full[stage]), ph, abort_flag, J.err, 2)) { ok = false; break; }
+                    if (!mbar_wait(smem_u32(&full[stage]), ph, abort_flag, J.err, 2, wait_ns)) { ok = false; break; }
                     fence_after();
                     const uint32_t sa = smem_base + (uint32_t)stage * stage_bytes;
                     const uint32_t sb = sa + 2 * G::A_PLANE;
@@ -365,7 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ T
             if (!ok && any) {
                 // wait (bounded) for every MMA issued so far before TMEM is released
                 mma_commit(smem_u32(drain));
-                mbar_drain(smem_u32(drain), 0);
+                mbar_drain(smem_u32(drain), 0, wait_ns);
             }
         }
         __syncwarp();
@@ -385,7 +395,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_leg_tc(const __grid_constant__ T
             const uint32_t acc_ph = (local >> 1) & 1;
             // every lane observes the barrier; the decision to stop is warp-uniform so
             // that the .sync.aligned TMEM loads below never run in a partial warp
-            const bool ok = mbar_wait(smem_u32(&tfull[acc]), acc_ph, abort_flag, J.err, 4);
+            const bool ok = mbar_wait(smem_u32(&tfull[acc]), acc_ph, abort_flag, J.err, 4, wait_ns);
             if (!__all_sync(0xffffffffu, ok)) break;
             fence_after();
             const int c = cm * TC_M + i;
@@ -509,10 +519,13 @@ st_status tc_job(st_plan *p, int dir, int nfields, void *data, void *out, TcJob 
 }
 
 template <int MAXJ>
-static st_status run_tc_batch(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s)
+static st_status run_tc_batch(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s, int withhold,
+                              unsigned long long wait_ns)
 {
     tc::TcBatch<MAXJ> B;  // copied into the kernel's parameters at launch
     B.njobs = n;
+    B.withhold_loads = withhold;
+    B.wait_ns = wait_ns;
     long long tot = 0;
     int max_nt = 16;
     for (int q = 0; q < n; ++q) {
@@ -542,12 +555,13 @@ static st_status run_tc_batch(int prec, const TcJob *jobs, int n, int sm_count, 
     return ST_OK;
 }
 
-st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s)
+st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s, int withhold,
+                         unsigned long long wait_ns)
 {
     if (n <= 0) return ST_OK;
     if (n > MAX_JOBS) return ST_ERR_ARG;
-    if (n == 1) return run_tc_batch<1>(prec, jobs, n, sm_count, s);
-    return run_tc_batch<MAX_JOBS>(prec, jobs, n, sm_count, s);
+    if (n == 1) return run_tc_batch<1>(prec, jobs, n, sm_count, s, withhold, wait_ns);
+    return run_tc_batch<MAX_JOBS>(prec, jobs, n, sm_count, s, withhold, wait_ns);
 }
 
 st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s, void *data_in, void *out_in)
@@ -557,7 +571,10 @@ st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s, void *
     TcJob J;
     st_status r = tc_job(p, dir, nfields, data, out, &J);
     if (r) return r;
-    return launch_tc_jobs(p->prec, &J, 1, p->sm_count, s);
+    const int withhold = p->inject_withhold;
+    const unsigned long long wait_ns = withhold ? p->inject_wait_ns : tc::WAIT_NS;
+    p->inject_withhold = 0;  // one launch only
+    return launch_tc_jobs(p->prec, &J, 1, p->sm_count, s, withhold, wait_ns);
 }
 
 }  // namespace st

@@ -248,6 +248,11 @@ struct st_plan {
     // freed when the last plan holding it is destroyed.
     std::shared_ptr<void> core;
 
+    // fault injection (tests): the next tensor-core Legendre launch withholds
+    // its operand copies and bounds its waits by inject_wait_ns
+    int inject_withhold = 0;
+    unsigned long long inject_wait_ns = 0;
+
     // launch accounting and optional event timing, per kernel kind
     bool timing = false;
     long long launches[16] = {0};
@@ -309,7 +314,8 @@ struct TcJob {
     int ncm, C, Cp, max_nt;
 };
 st_status tc_job(st_plan *p, int dir, int nfields, void *data, void *out, TcJob *job);
-st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s);
+st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s, int withhold = 0,
+                         unsigned long long wait_ns = 2000000000ull);
 
 // ---- launchers implemented in the .cu files ----
 st_status launch_tables(st_plan *p, cudaStream_t s);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "st_plan_create": [ctypes.POINTER(_VP), _I, ctypes.POINTER(_GridDesc), _I, _I, _VP],
     "st_plan_destroy": [_VP],
     "st_plan_create_shared": [ctypes.POINTER(_VP), _VP, _I, _VP],
+    "st_plan_inject": [_VP, _I, ctypes.c_uint],
     "st_plan_query": [_VP, ctypes.POINTER(_PlanInfo)],
     "st_plan_row_lengths": [_VP, ctypes.POINTER(ctypes.c_int)],
     "st_plan_nodes": [_VP, _D, _D],

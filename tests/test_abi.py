@@ -63,6 +63,10 @@ def test_argument_errors_without_device(st_mod):
     assert lib.st_gauss_nodes(1, None, None, None) == ST_ERR_ARG
     assert lib.st_legendre_values(-1, None, 1, None, None) == ST_ERR_ARG
     assert lib.st_status_string(4) == b"device-side wait timed out"
+    assert lib.st_plan_inject(None, 1, 100) == ST_ERR_ARG
+    assert lib.st_plan_create_shared(None, None, 1, None) == ST_ERR_ARG
+    assert lib.st_batch_create(None, None, 0) == ST_ERR_ARG
+    assert lib.st_inv_trans_static(None, None, None, 1, None) == ST_ERR_ARG
 
 
 def test_product_path_does_not_import_the_oracle():

@@ -1,0 +1,59 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times (all fields in one call), on fields the oracle computes one by one:
+
+  T639 on O640 (1280 latitudes, rows 20 + 4i), 548 fields, BF16x3, spectra
+  N(0,1) (n+1)^-1.5 — fields 0, 273 and 547;
+  T159 on the regular 160 x 320 grid, 411 fields, FP64 and 3xTF32 — fields
+  0 and 410.
+
+Inverse: GPU grid of the sampled fields vs the oracle's synthesis of the same
+spectra.  Direct: the sampled fields' grids are replaced by the oracle's
+(band-limited) grids before the GPU direct transform of the whole batch; GPU
+spectra of those fields vs the oracle's analysis of the same grids.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1908_06096_gb300 import inputs
+from tests.conftest import per_field_max_rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "tf32x3": 2e-5, "bf16x3": 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+CASES = [
+    (639, "octahedral", 1280, 0, 548, 1.5, 1002, "bf16x3", (0, 273, 547)),
+    (159, "regular", 160, 320, 411, 1.0, 1001, "fp64", (0, 410)),
+    (159, "regular", 160, 320, 411, 1.0, 1001, "tf32x3", (0, 410)),
+]
+
+
+@pytest.mark.parametrize("T,grid,nlat,nlon,F,pdec,seed,prec,sample", CASES)
+def test_full_size_sampled_fields(st_mod, oracle_mod, T, grid, nlat, nlon, F, pdec, seed, prec, sample):
+    a = inputs.spectra(T, F, seed=seed, p=pdec)
+    plan = st_mod.Plan(T, grid, nlat=nlat, nlon=nlon or None, precision=prec, max_fields=F)
+    dt = plan.dtype
+    g = plan.inv(torch.from_numpy(a).to("cuda", dt))
+    rows = oracle_mod.grid_rows(grid, nlat, nlon)
+    mu, w = oracle_mod.gauss(nlat)
+    idx = list(sample)
+    g_ref = oracle_mod.inv_trans(T, rows, mu, a[idx])
+    g_gpu = g[idx].double().cpu().numpy()
+    assert per_field_max_rel(g_gpu, g_ref) < TOL[prec]
+    # direct: put the oracle's grids into the sampled slots of the batch
+    g_in = g.clone()
+    g_in[idx] = torch.from_numpy(g_ref).to("cuda", dt)
+    s = plan.dir(g_in)
+    plan.sync()
+    s_ref = oracle_mod.dir_trans(T, rows, mu, w, g_in[idx].double().cpu().numpy())
+    s_gpu = s[idx].double().cpu().numpy()
+    assert per_field_max_rel(s_gpu[..., 0] + 1j * s_gpu[..., 1], s_ref) < TOL[prec]
+    plan.close()
