@@ -32,7 +32,13 @@
 
 namespace st {
 
-constexpr int FFT_THREADS = 256;
+#ifndef ST_FFT_THREADS
+#define ST_FFT_THREADS 256
+#endif
+#ifndef ST_FFT_MINB
+#define ST_FFT_MINB 2
+#endif
+constexpr int FFT_THREADS = ST_FFT_THREADS;
 
 template <typename R> struct CT;
 template <> struct CT<double> { typedef double2 T; };
@@ -135,11 +141,15 @@ template <int R, typename C> __device__ inline void dftR(C *v)
 // and forms its powers by multiplication.  Element i of a field lives at
 // shared-memory slot Swz(i).
 
+template <int MODE>
 struct Swz {
-    int a, pm, xm;
-    __device__ explicit Swz(int mode)
-        : a(mode == 2 ? 5 : 4), pm((mode == 1 || mode == 2) ? -1 : 0), xm(mode == 3 ? 15 : 0) {}
-    __device__ int operator()(int i) const { return (i + ((i >> a) & pm)) ^ ((i >> 4) & xm); }
+    __device__ int operator()(int i) const
+    {
+        if (MODE == 1) return i + (i >> 4);
+        if (MODE == 2) return i + (i >> 5);
+        if (MODE == 3) return i ^ ((i >> 4) & 15);
+        return i;
+    }
 };
 
 // n / d for 0 <= n < 2^22 without an integer divide: float reciprocal, then
@@ -169,8 +179,8 @@ template <int R, typename C> __device__ inline void twiddle_powers(C *v, C w)
     }
 }
 
-template <int Ra, int Rb, bool DIT, typename C>
-__device__ inline void pass2(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, Swz sw,
+template <int Ra, int Rb, bool DIT, typename C, class SW>
+__device__ inline void pass2(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, SW sw,
                              const C *__restrict__ kern)
 {
     const int ma = Ns / Ra, mb = ma / Rb;
@@ -243,8 +253,8 @@ __device__ inline void pass2(C *x, const C *__restrict__ tw, int L, int S, int N
     }
 }
 
-template <int R, bool DIT, typename C>
-__device__ inline void pass1(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, Swz sw,
+template <int R, bool DIT, typename C, class SW>
+__device__ inline void pass1(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, SW sw,
                              const C *__restrict__ kern)
 {
     const int m = Ns / R;
@@ -276,24 +286,24 @@ __device__ inline void pass1(C *x, const C *__restrict__ tw, int L, int S, int N
     }
 }
 
-template <bool DIT, typename C>
-__device__ inline void run_pass2(int Ra, int Rb, C *x, const C *tw, int L, int S, int Ns, int G, Swz sw,
+template <bool DIT, typename C, class SW>
+__device__ inline void run_pass2(int Ra, int Rb, C *x, const C *tw, int L, int S, int Ns, int G, SW sw,
                                  const C *kern)
 {
 #define ST_P2(A, B) \
-    if (Ra == A && Rb == B) { pass2<A, B, DIT, C>(x, tw, L, S, Ns, G, sw, kern); return; }
+    if (Ra == A && Rb == B) { pass2<A, B, DIT, C, SW>(x, tw, L, S, Ns, G, sw, kern); return; }
     ST_P2(4, 4) ST_P2(4, 3) ST_P2(3, 4) ST_P2(3, 3) ST_P2(4, 2) ST_P2(2, 4) ST_P2(3, 5) ST_P2(5, 3)
     ST_P2(2, 5) ST_P2(5, 2) ST_P2(2, 3) ST_P2(3, 2) ST_P2(2, 2)
 #undef ST_P2
 }
 
-template <bool DIT, typename C>
-__device__ inline void run_pass1(int R, C *x, const C *tw, int L, int S, int Ns, int G, Swz sw, const C *kern)
+template <bool DIT, typename C, class SW>
+__device__ inline void run_pass1(int R, C *x, const C *tw, int L, int S, int Ns, int G, SW sw, const C *kern)
 {
-    if (R == 2) pass1<2, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
-    else if (R == 3) pass1<3, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
-    else if (R == 4) pass1<4, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
-    else pass1<5, DIT, C>(x, tw, L, S, Ns, G, sw, kern);
+    if (R == 2) pass1<2, DIT, C, SW>(x, tw, L, S, Ns, G, sw, kern);
+    else if (R == 3) pass1<3, DIT, C, SW>(x, tw, L, S, Ns, G, sw, kern);
+    else if (R == 4) pass1<4, DIT, C, SW>(x, tw, L, S, Ns, G, sw, kern);
+    else pass1<5, DIT, C, SW>(x, tw, L, S, Ns, G, sw, kern);
 }
 
 // Stages are fused in pairs when the pair holds at most 16 points (the
@@ -302,21 +312,21 @@ constexpr int MAX_FUSED = 16;
 
 // All DIF stages over rp.rad (natural -> digit-reversed).  With `kern`, the
 // last pass also multiplies by the kernel spectrum and conjugates.
-template <typename C>
+template <typename C, class SW>
 __device__ void fft_dif(C *x, const C *tw, const RowPair &rp, int G, int S, const C *kern)
 {
     const int L = rp.fftlen;
-    const Swz sw(rp.swz);
+    const SW sw;
     int Ns = L;
     for (int q = 0; q < rp.nrad;) {
         if (q + 1 < rp.nrad && rp.rad[q] * rp.rad[q + 1] <= MAX_FUSED) {
             const bool last = q + 2 >= rp.nrad;
-            run_pass2<false, C>(rp.rad[q], rp.rad[q + 1], x, tw, L, S, Ns, G, sw, last ? kern : nullptr);
+            run_pass2<false, C, SW>(rp.rad[q], rp.rad[q + 1], x, tw, L, S, Ns, G, sw, last ? kern : nullptr);
             Ns /= rp.rad[q] * rp.rad[q + 1];
             q += 2;
         } else {
             const bool last = q + 1 >= rp.nrad;
-            run_pass1<false, C>(rp.rad[q], x, tw, L, S, Ns, G, sw, last ? kern : nullptr);
+            run_pass1<false, C, SW>(rp.rad[q], x, tw, L, S, Ns, G, sw, last ? kern : nullptr);
             Ns /= rp.rad[q];
             q += 1;
         }
@@ -325,20 +335,20 @@ __device__ void fft_dif(C *x, const C *tw, const RowPair &rp, int G, int S, cons
 }
 
 // All DIT stages (digit-reversed -> natural): the stages in reverse order.
-template <typename C>
+template <typename C, class SW>
 __device__ void fft_dit(C *x, const C *tw, const RowPair &rp, int G, int S)
 {
     const int L = rp.fftlen;
-    const Swz sw(rp.swz);
+    const SW sw;
     int Ns = 1;
     for (int q = rp.nrad - 1; q >= 0;) {
         if (q >= 1 && rp.rad[q - 1] * rp.rad[q] <= MAX_FUSED) {
             Ns *= rp.rad[q - 1] * rp.rad[q];
-            run_pass2<true, C>(rp.rad[q - 1], rp.rad[q], x, tw, L, S, Ns, G, sw, (const C *)nullptr);
+            run_pass2<true, C, SW>(rp.rad[q - 1], rp.rad[q], x, tw, L, S, Ns, G, sw, (const C *)nullptr);
             q -= 2;
         } else {
             Ns *= rp.rad[q];
-            run_pass1<true, C>(rp.rad[q], x, tw, L, S, Ns, G, sw, (const C *)nullptr);
+            run_pass1<true, C, SW>(rp.rad[q], x, tw, L, S, Ns, G, sw, (const C *)nullptr);
             q -= 1;
         }
         __syncthreads();
@@ -348,17 +358,17 @@ __device__ void fft_dit(C *x, const C *tw, const RowPair &rp, int G, int S)
 // Forward N-point DFT of each field's sequence, already in x (mode 0: natural
 // order; mode 1: premultiplied by the chirp and zero up to L).  Afterwards
 // fft_value(m) gives Z_m.
-template <typename C>
+template <typename C, class SW>
 __device__ inline void fft_forward(C *x, const C *tw, const C *__restrict__ kern, const RowPair &rp, int G, int S)
 {
-    fft_dif<C>(x, tw, rp, G, S, rp.mode == 1 ? kern : nullptr);
-    if (rp.mode == 1) fft_dit<C>(x, tw, rp, G, S);
+    fft_dif<C, SW>(x, tw, rp, G, S, rp.mode == 1 ? kern : nullptr);
+    if (rp.mode == 1) fft_dit<C, SW>(x, tw, rp, G, S);
 }
 
-template <typename C>
+template <typename C, class SW>
 __device__ inline C fft_value(const C *xf, const C *__restrict__ chirp, const RowPair &rp, int m)
 {
-    const Swz sw(rp.swz);
+    const SW sw;
     if (rp.mode == 0) return xf[sw(dif_pos(m, rp))];
     return cmul(__ldg(&chirp[m]), cconj(xf[sw(m)]));
 }
@@ -415,20 +425,24 @@ __device__ inline void store_pair(void *base, long long r, int c, int Cp, long l
     }
 }
 
-template <typename Rr> struct FftBounds { static constexpr int MINB = 3; };
+template <typename Rr> struct FftBounds { static constexpr int MINB = ST_FFT_MINB; };
 template <> struct FftBounds<double> { static constexpr int MINB = 1; };
 
-template <typename Rr, int S, int MAXJ>
-__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_dir(const __grid_constant__ FftBatch<MAXJ> B)
+// The row's metadata is copied once per CTA into shared memory (a per-thread
+// copy would live in local memory: the radix list is indexed at run time).
+__device__ inline void load_rowpair(RowPair *dst, const RowPair *src)
+{
+    const int nw = (int)(sizeof(RowPair) / sizeof(int));
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) ((int *)dst)[i] = ((const int *)src)[i];
+    __syncthreads();
+}
+
+template <typename Rr, int S, class SW>
+__device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, int f0)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
-    const FftJob &J = B.job[q];
-    const int b = (int)(blockIdx.x - B.prefix[q]);
-    const int j = b / J.nfg, G = J.G;
-    const int f0 = (b - j * J.nfg) * G;
-    const RowPair rp = J.rps[j];
+    const int G = J.G;
     const int N = rp.N, W = rp.fftlen, SL = J.Sslot;
     const int nfields = J.nfields, Cp = J.Cp, T = J.T, Jp = J.Jp;
     const long long npts = J.npts, Rp = J.Rp, plane_stride = J.ps;
@@ -437,25 +451,25 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_dir(co
     C *x = (C *)smem_raw;
     const C *tw = (const C *)J.tw + rp.tw_off;
     const C *chirp = (const C *)J.chirp + rp.chirp_off;
-    const Swz sw(rp.swz);
+    const SW sw;
 
-    const FastDiv dW(W);
-    for (int idx = threadIdx.x; idx < G * W; idx += blockDim.x) {
-        const int f = dW(idx), k = idx - f * W;
+    for (int f = 0; f < G; ++f) {
         const int fld = f0 + f;
-        C v;
-        v.x = 0;
-        v.y = 0;
-        if (fld < nfields && k < N) {
-            const Rr *g = grid + (long long)fld * npts;
-            v.x = g[rp.off_n + k];
-            v.y = g[rp.off_s + k];
-            if (rp.mode == 1) v = cmul(v, __ldg(&chirp[k]));
+        const Rr *g = grid + (long long)fld * npts;
+        for (int k = threadIdx.x; k < W; k += blockDim.x) {
+            C v;
+            v.x = 0;
+            v.y = 0;
+            if (fld < nfields && k < N) {
+                v.x = g[rp.off_n + k];
+                v.y = g[rp.off_s + k];
+                if (rp.mode == 1) v = cmul(v, __ldg(&chirp[k]));
+            }
+            x[(size_t)f * SL + sw(k)] = v;
         }
-        x[(size_t)f * SL + sw(k)] = v;
     }
     __syncthreads();
-    fft_forward<C>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, SL);
+    fft_forward<C, SW>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, SL);
 
     const Rr inv = (Rr)1.0 / (Rr)N;
     const int M = rp.M;
@@ -465,8 +479,8 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_dir(co
         const int fld = f0 + f;
         if (fld >= nfields) continue;
         const C *xf = x + (size_t)f * SL;
-        C zm = fft_value<C>(xf, chirp, rp, m);
-        C zc = cconj(m == 0 ? zm : fft_value<C>(xf, chirp, rp, N - m));
+        C zm = fft_value<C, SW>(xf, chirp, rp, m);
+        C zc = cconj(m == 0 ? zm : fft_value<C, SW>(xf, chirp, rp, N - m));
         // north spectrum A = (zm + zc)/2, south spectrum B = -i (zm - zc)/2
         Rr ax = (zm.x + zc.x) * (Rr)0.5, ay = (zm.y + zc.y) * (Rr)0.5;
         Rr dx = (zm.x - zc.x) * (Rr)0.5, dy = (zm.y - zc.y) * (Rr)0.5;
@@ -480,18 +494,31 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_dir(co
     }
 }
 
-template <typename Rr, int MAXJ>
-__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_inv(const __grid_constant__ FftBatch<MAXJ> B)
+template <typename Rr, int S, int MAXJ>
+__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_dir(const __grid_constant__ FftBatch<MAXJ> B)
+{
+    __shared__ RowPair rp;
+    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
+    const FftJob &J = B.job[q];
+    const int b = (int)(blockIdx.x - B.prefix[q]);
+    const int j = b / J.nfg;
+    const int f0 = (b - j * J.nfg) * J.G;
+    load_rowpair(&rp, J.rps + j);
+    switch (rp.swz) {
+    case 1: fft_dir_body<Rr, S, Swz<1>>(J, rp, j, f0); break;
+    case 2: fft_dir_body<Rr, S, Swz<2>>(J, rp, j, f0); break;
+    case 3: fft_dir_body<Rr, S, Swz<3>>(J, rp, j, f0); break;
+    default: fft_dir_body<Rr, S, Swz<0>>(J, rp, j, f0); break;
+    }
+}
+
+template <typename Rr, class SW>
+__device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, int f0)
 {
     typedef typename CT<Rr>::T C;
     typedef typename CT<Rr>::T C2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
-    const FftJob &J = B.job[q];
-    const int b = (int)(blockIdx.x - B.prefix[q]);
-    const int j = b / J.nfg, G = J.G;
-    const int f0 = (b - j * J.nfg) * G;
-    const RowPair rp = J.rps[j];
+    const int G = J.G;
     const int N = rp.N, S = J.Sslot;
     const int nfields = J.nfields, Cp = J.Cp, T = J.T, Jp = J.Jp;
     const long long npts = J.npts;
@@ -500,7 +527,7 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_inv(co
     C *x = (C *)smem_raw;
     const C *tw = (const C *)J.tw + rp.tw_off;
     const C *chirp = (const C *)J.chirp + rp.chirp_off;
-    const Swz sw(rp.swz);
+    const SW sw;
 
     for (int idx = threadIdx.x; idx < G * S; idx += blockDim.x) {
         C v;
@@ -551,16 +578,35 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_inv(co
         }
     }
     __syncthreads();
-    fft_forward<C>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, S);
-    const FastDiv dN(N);
-    for (int idx = threadIdx.x; idx < G * N; idx += blockDim.x) {
-        const int f = dN(idx), k = idx - f * N;
+    fft_forward<C, SW>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, S);
+    for (int f = 0; f < G; ++f) {
         const int fld = f0 + f;
-        if (fld >= nfields) continue;
-        const C v = fft_value<C>(x + (size_t)f * S, chirp, rp, k);
+        if (fld >= nfields) break;
         Rr *g = grid + (long long)fld * npts;
-        g[rp.off_n + k] = v.x;
-        g[rp.off_s + k] = -v.y;
+        const C *xf = x + (size_t)f * S;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const C v = fft_value<C, SW>(xf, chirp, rp, k);
+            g[rp.off_n + k] = v.x;
+            g[rp.off_s + k] = -v.y;
+        }
+    }
+}
+
+template <typename Rr, int MAXJ>
+__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_inv(const __grid_constant__ FftBatch<MAXJ> B)
+{
+    __shared__ RowPair rp;
+    const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
+    const FftJob &J = B.job[q];
+    const int b = (int)(blockIdx.x - B.prefix[q]);
+    const int j = b / J.nfg;
+    const int f0 = (b - j * J.nfg) * J.G;
+    load_rowpair(&rp, J.rps + j);
+    switch (rp.swz) {
+    case 1: fft_inv_body<Rr, Swz<1>>(J, rp, j, f0); break;
+    case 2: fft_inv_body<Rr, Swz<2>>(J, rp, j, f0); break;
+    case 3: fft_inv_body<Rr, Swz<3>>(J, rp, j, f0); break;
+    default: fft_inv_body<Rr, Swz<0>>(J, rp, j, f0); break;
     }
 }
 
@@ -570,7 +616,10 @@ static int fft_fields_per_cta(const st_plan *p, int nfields, size_t *smem)
 {
     const size_t cs = p->prec == P_FP64 ? 16 : 8;
     const size_t per = (size_t)p->max_fft_smem * cs;
-    const size_t budget = p->prec == P_FP64 ? 110 * 1024 : 56 * 1024;
+#ifndef ST_FFT_SMEM_KB
+#define ST_FFT_SMEM_KB 100
+#endif
+    const size_t budget = p->prec == P_FP64 ? 110 * 1024 : ST_FFT_SMEM_KB * 1024;
     int G = (int)(budget / per);
     if (G < 1) G = 1;
     if (G > 8) G = 8;
