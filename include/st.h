@@ -91,6 +91,8 @@ typedef struct {
     size_t device_bytes;      /* device memory held by the plan */
     size_t table_bytes;       /* of which Legendre tables */
     size_t workspace_bytes;   /* of which workspace */
+    int launch_shape[5];      /* inverse FFT variant, its smem budget (KB), direct FFT variant, its
+                                 budget (KB), inverse Legendre column-tile width (0: automatic) */
 } st_plan_info;
 
 /*
@@ -119,6 +121,20 @@ st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int pr
  * resident while several requests of that truncation are in flight.
  */
 st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, void *stream);
+
+/*
+ * Autotuner (not in the paper; SURVEY-level "per-m tile shapes picked by an
+ * autotuner").  Times, on this plan and for `nfields` fields, candidate FFT
+ * launch shapes (threads per CTA, CTAs per SM, fields per CTA) for each
+ * direction and, on tensor-core plans, candidate column-tile widths of the
+ * inverse per-m Legendre GEMMs (re-laying out the tables), and keeps the
+ * fastest.  Synchronous; allocates a temporary grid buffer.  If cache_path is
+ * not NULL the choice is appended to that text file; st_plan_create applies a
+ * matching entry (same T, grid, precision, field-count bucket and SM count)
+ * from the file named by the ST_TUNE_CACHE environment variable.
+ * ST_ERR_BUSY if the plan shares its tables with another plan.
+ */
+st_status st_plan_autotune(st_plan_t plan, int nfields, const char *cache_path, void *stream);
 
 /* Release everything the plan holds.  NULL is accepted.  The caller must make
  * sure no work on the plan is still in flight. */

@@ -186,9 +186,14 @@ static void build_groups(st_plan *p, int dir)
     const int T = p->T, J = p->J;
     const bool tc = prec_is_tc(p->prec);
     const int kc = tc ? tc_kc(p->prec) : 1;
-    // inverse column tile: the table columns are the J northern rows
+    // inverse column tile: the table columns are the J northern rows; width
+    // from the autotuner if it chose one, else the fewest tiles of <= 256
     int nct_inv = (J + 255) / 256;
     int nt_inv = ((J + nct_inv - 1) / nct_inv + 15) / 16 * 16;
+    if (p->nt_inv > 0) {
+        nt_inv = std::min(p->nt_inv, (J + 15) / 16 * 16);
+        nct_inv = (J + nt_inv - 1) / nt_inv;
+    }
 
     std::vector<LegGroup> &G = p->groups_h[dir];
     G.assign(2 * (T + 1), LegGroup{});
@@ -294,11 +299,90 @@ static st_status alloc_workspace(st_plan *p, cudaStream_t s)
     return ST_OK;
 }
 
+// Rebuild the Legendre groups, work lists and tables of both directions with
+// the plan's current tile choices (used by the autotuner).  The plan must not
+// share its tables with another plan.
+st_status rebuild_legendre(st_plan *p, cudaStream_t s)
+{
+    TableCore *core = (TableCore *)p->core.get();
+    if (!core || p->core.use_count() != 1) return ST_ERR_BUSY;
+    ST_CUDA(cudaStreamSynchronize(s));
+    for (int dir = 0; dir < 2; ++dir) {
+        void *old[3] = {p->tab[dir], p->groups[dir], p->tiles[dir]};
+        for (void *q : old) {
+            if (!q) continue;
+            cudaFree(q);
+            for (auto &c : core->ptrs)
+                if (c == q) c = nullptr;
+        }
+        p->tab[dir] = nullptr;
+        p->groups[dir] = nullptr;
+        p->tiles[dir] = nullptr;
+    }
+    p->table_bytes = 0;
+    st_status r;
+    for (int dir = 0; dir < 2; ++dir) {
+        build_groups(p, dir);
+        std::vector<LegTile> tl = build_tiles(p, dir);
+        p->ntiles[dir] = (int)tl.size();
+        if ((r = dmalloc(p, &p->groups[dir], sizeof(LegGroup) * p->groups_h[dir].size()))) return r;
+        ST_CUDA(cudaMemcpy(p->groups[dir], p->groups_h[dir].data(), sizeof(LegGroup) * p->groups_h[dir].size(),
+                           cudaMemcpyHostToDevice));
+        if ((r = dmalloc(p, &p->tiles[dir], sizeof(LegTile) * std::max<size_t>(tl.size(), 1)))) return r;
+        if (!tl.empty())
+            ST_CUDA(cudaMemcpy(p->tiles[dir], tl.data(), sizeof(LegTile) * tl.size(), cudaMemcpyHostToDevice));
+        if ((r = dmalloc(p, &p->tab[dir], p->tab_bytes[dir]))) return r;
+        ST_CUDA(cudaMemsetAsync(p->tab[dir], 0, std::max<size_t>(p->tab_bytes[dir], 16), s));
+        p->table_bytes += p->tab_bytes[dir];
+        core->ptrs.push_back(p->tab[dir]);
+        core->ptrs.push_back(p->groups[dir]);
+        core->ptrs.push_back(p->tiles[dir]);
+    }
+    if ((r = launch_tables(p, s))) return r;
+    ST_CUDA(cudaStreamSynchronize(s));
+    return ST_OK;
+}
+
+std::string tune_key(const st_plan *p, int nfields)
+{
+    int b = 1;
+    while (b < nfields) b <<= 1;
+    return std::to_string(p->T) + " " + std::to_string(p->nlat) + " " + std::to_string(p->kind) + " " +
+           std::to_string(p->nlon) + " " + std::to_string(p->prec) + " " + std::to_string(b) + " " +
+           std::to_string(p->sm_count);
+}
+
+// Apply a cached autotuner choice (file named by ST_TUNE_CACHE) for this
+// plan's key, if there is one.
+static void apply_tune_cache(st_plan *p)
+{
+    const char *path = getenv("ST_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    const std::string key = tune_key(p, p->max_fields);
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        std::string l(line);
+        if (l.compare(0, key.size() + 1, key + " ") != 0) continue;
+        int v0, k0, v1, k1, nt;
+        if (sscanf(l.c_str() + key.size() + 1, "| %d %d %d %d %d", &v0, &k0, &v1, &k1, &nt) == 5) {
+            p->fft_var[0] = v0;
+            p->fft_kb[0] = k0;
+            p->fft_var[1] = v1;
+            p->fft_kb[1] = k1;
+            p->nt_inv = nt;
+        }
+    }
+    fclose(f);
+}
+
 static st_status plan_build(st_plan *p, cudaStream_t s)
 {
     const int T = p->T, nlat = p->nlat, J = nlat / 2;
     p->J = J;
     p->Jp = (int)rows_padded(J);
+    apply_tune_cache(p);
     p->rows.resize(nlat);
     for (int j = 0; j < nlat; ++j) {
         if (p->kind == ST_GRID_REGULAR) p->rows[j] = p->nlon;
@@ -607,6 +691,8 @@ st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, 
     p->rowpairs_h = base->rowpairs_h; p->tw = base->tw; p->ntw = base->ntw; p->chirp = base->chirp;
     p->kern = base->kern; p->nchirp = base->nchirp; p->nkern = base->nkern; p->max_row = base->max_row;
     p->max_fft = base->max_fft; p->max_chirp = base->max_chirp; p->max_fft_smem = base->max_fft_smem;
+    p->fft_var[0] = base->fft_var[0]; p->fft_var[1] = base->fft_var[1];
+    p->fft_kb[0] = base->fft_kb[0]; p->fft_kb[1] = base->fft_kb[1]; p->nt_inv = base->nt_inv;
     for (int d = 0; d < 2; ++d) {
         p->tab[d] = base->tab[d];
         p->tab_bytes[d] = base->tab_bytes[d];
@@ -652,6 +738,11 @@ st_status st_plan_query(st_plan_t p, st_plan_info *info)
     info->device_bytes = p->device_bytes;
     info->table_bytes = p->table_bytes;
     info->workspace_bytes = p->workspace_bytes;
+    info->launch_shape[0] = p->fft_var[0];
+    info->launch_shape[1] = p->fft_kb[0];
+    info->launch_shape[2] = p->fft_var[1];
+    info->launch_shape[3] = p->fft_kb[1];
+    info->launch_shape[4] = p->nt_inv;
     return ST_OK;
 }
 

@@ -17,6 +17,8 @@ struct st_batch {
         std::vector<long long> simt_inv_blocks, simt_dir_blocks;
         std::vector<FftJob> fft_inv, fft_dir;
         size_t smem_inv = 0, smem_dir = 0;
+        int var_inv = 0, var_dir = 0;  // launch variant of the largest job
+        long long big_inv = -1, big_dir = -1;
     };
     std::map<int, Stage> by_prec;
     int sm_count = 0;
@@ -53,7 +55,7 @@ st_status batch_launch(st_batch *b, cudaStream_t s)
              })))
             return r;
         if ((r = chunked(S.fft_inv, [&](const FftJob *j, int n, size_t) {
-                 return launch_fft_jobs(0, prec, j, n, S.smem_inv, s);
+                 return launch_fft_jobs(0, prec, j, n, S.smem_inv, s, S.var_inv);
              })))
             return r;
     }
@@ -61,7 +63,7 @@ st_status batch_launch(st_batch *b, cudaStream_t s)
         const int prec = kv.first;
         auto &S = kv.second;
         if ((r = chunked(S.fft_dir, [&](const FftJob *j, int n, size_t) {
-                 return launch_fft_jobs(1, prec, j, n, S.smem_dir, s);
+                 return launch_fft_jobs(1, prec, j, n, S.smem_dir, s, S.var_dir);
              })))
             return r;
         if ((r = chunked(S.tc_dir, [&](const TcJob *j, int n, size_t) { return launch_tc_jobs(prec, j, n, b->sm_count, s); })))
@@ -125,6 +127,7 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n)
             if ((r = fft_job(p, 0, it.nfields, p->fb, it.grid, &fj, &smem))) { delete b; return r; }
             S.fft_inv.push_back(fj);
             S.smem_inv = std::max(S.smem_inv, smem);
+            if ((long long)fj.J * fj.nfg > S.big_inv) { S.big_inv = (long long)fj.J * fj.nfg; S.var_inv = p->fft_var[0]; }
         }
         if (it.direction != 0) {
             FftJob fj;
@@ -132,6 +135,7 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n)
             if ((r = fft_job(p, 1, it.nfields, it.grid, p->fbop, &fj, &smem))) { delete b; return r; }
             S.fft_dir.push_back(fj);
             S.smem_dir = std::max(S.smem_dir, smem);
+            if ((long long)fj.J * fj.nfg > S.big_dir) { S.big_dir = (long long)fj.J * fj.nfg; S.var_dir = p->fft_var[1]; }
             if (prec_is_tc(p->prec)) {
                 TcJob tj;
                 if ((r = tc_job(p, 1, it.nfields, p->fbop, p->sout, &tj))) { delete b; return r; }

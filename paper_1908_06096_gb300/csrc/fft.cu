@@ -32,13 +32,12 @@
 
 namespace st {
 
-#ifndef ST_FFT_THREADS
-#define ST_FFT_THREADS 256
-#endif
-#ifndef ST_FFT_MINB
-#define ST_FFT_MINB 2
-#endif
-constexpr int FFT_THREADS = ST_FFT_THREADS;
+// Launch variants the autotuner chooses between: threads per CTA and the
+// minimum number of CTAs per SM the register allocation is sized for.
+// (FP64 kernels always use variant 0 with one CTA per SM guaranteed.)
+constexpr int FFT_VARIANTS = 2;
+constexpr int FFT_VAR_THREADS[FFT_VARIANTS] = {256, 128};
+constexpr int FFT_VAR_MINB[FFT_VARIANTS] = {2, 4};
 
 template <typename R> struct CT;
 template <> struct CT<double> { typedef double2 T; };
@@ -425,8 +424,8 @@ __device__ inline void store_pair(void *base, long long r, int c, int Cp, long l
     }
 }
 
-template <typename Rr> struct FftBounds { static constexpr int MINB = ST_FFT_MINB; };
-template <> struct FftBounds<double> { static constexpr int MINB = 1; };
+template <typename Rr, int MB> struct FftBounds { static constexpr int MINB = MB; };
+template <int MB> struct FftBounds<double, MB> { static constexpr int MINB = 1; };
 
 // The row's metadata is copied once per CTA into shared memory (a per-thread
 // copy would live in local memory: the radix list is indexed at run time).
@@ -494,8 +493,8 @@ __device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, i
     }
 }
 
-template <typename Rr, int S, int MAXJ>
-__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_dir(const __grid_constant__ FftBatch<MAXJ> B)
+template <typename Rr, int S, int MAXJ, int NT, int MB>
+__global__ void __launch_bounds__(NT, (FftBounds<Rr, MB>::MINB)) k_fft_dir(const __grid_constant__ FftBatch<MAXJ> B)
 {
     __shared__ RowPair rp;
     const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
@@ -592,8 +591,8 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
     }
 }
 
-template <typename Rr, int MAXJ>
-__global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_inv(const __grid_constant__ FftBatch<MAXJ> B)
+template <typename Rr, int MAXJ, int NT, int MB>
+__global__ void __launch_bounds__(NT, (FftBounds<Rr, MB>::MINB)) k_fft_inv(const __grid_constant__ FftBatch<MAXJ> B)
 {
     __shared__ RowPair rp;
     const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
@@ -611,15 +610,12 @@ __global__ void __launch_bounds__(FFT_THREADS, FftBounds<Rr>::MINB) k_fft_inv(co
 }
 
 // Fields per CTA: one shared-memory buffer of fftlen complex values each,
-// within a per-CTA budget that leaves room for several CTAs per SM.
-static int fft_fields_per_cta(const st_plan *p, int nfields, size_t *smem)
+// within the plan's per-CTA budget for this direction (autotuned).
+static int fft_fields_per_cta(const st_plan *p, int dir, int nfields, size_t *smem)
 {
     const size_t cs = p->prec == P_FP64 ? 16 : 8;
     const size_t per = (size_t)p->max_fft_smem * cs;
-#ifndef ST_FFT_SMEM_KB
-#define ST_FFT_SMEM_KB 100
-#endif
-    const size_t budget = p->prec == P_FP64 ? 110 * 1024 : ST_FFT_SMEM_KB * 1024;
+    const size_t budget = p->prec == P_FP64 ? 110 * 1024 : (size_t)p->fft_kb[dir] * 1024;
     int G = (int)(budget / per);
     if (G < 1) G = 1;
     if (G > 8) G = 8;
@@ -646,7 +642,7 @@ st_status fft_job(st_plan *p, int dir, int nfields, const void *src, void *dst, 
     J.dst = dst;
     J.npts = p->npts;
     J.nfields = nfields;
-    J.G = fft_fields_per_cta(p, nfields, smem);
+    J.G = fft_fields_per_cta(p, dir, nfields, smem);
     J.Sslot = p->max_fft_smem;
     J.Cp = cols_padded(nfields);
     J.Rp = fb_rows(p);
@@ -660,7 +656,7 @@ st_status fft_job(st_plan *p, int dir, int nfields, const void *src, void *dst, 
 }
 
 template <int MAXJ, class K>
-static st_status run_fft_batch(K kern, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
+static st_status run_fft_batch(K kern, int threads, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
 {
     FftBatch<MAXJ> B;
     B.njobs = n;
@@ -675,34 +671,45 @@ static st_status run_fft_batch(K kern, const FftJob *jobs, int n, size_t smem, c
     if (tot > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
     st_status r = set_smem(kern, smem);
     if (r) return r;
-    kern<<<(unsigned)tot, FFT_THREADS, smem, s>>>(B);
+    kern<<<(unsigned)tot, threads, smem, s>>>(B);
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }
 
-template <int MAXJ>
-static st_status launch_fft_jobs_t(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
+template <int MAXJ, int NT, int MB>
+static st_status launch_fft_jobs_v(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
 {
     if (dir == 1) {
         switch (prec) {
-        case P_FP64: return run_fft_batch<MAXJ>(k_fft_dir<double, S_F64, MAXJ>, jobs, n, smem, s);
-        case P_FP32: return run_fft_batch<MAXJ>(k_fft_dir<float, S_F32, MAXJ>, jobs, n, smem, s);
-        case P_TF32X3: return run_fft_batch<MAXJ>(k_fft_dir<float, S_TF32_SPLIT, MAXJ>, jobs, n, smem, s);
-        default: return run_fft_batch<MAXJ>(k_fft_dir<float, S_BF16_SPLIT, MAXJ>, jobs, n, smem, s);
+        case P_FP64: return run_fft_batch<MAXJ>(k_fft_dir<double, S_F64, MAXJ, NT, MB>, NT, jobs, n, smem, s);
+        case P_FP32: return run_fft_batch<MAXJ>(k_fft_dir<float, S_F32, MAXJ, NT, MB>, NT, jobs, n, smem, s);
+        case P_TF32X3:
+            return run_fft_batch<MAXJ>(k_fft_dir<float, S_TF32_SPLIT, MAXJ, NT, MB>, NT, jobs, n, smem, s);
+        default: return run_fft_batch<MAXJ>(k_fft_dir<float, S_BF16_SPLIT, MAXJ, NT, MB>, NT, jobs, n, smem, s);
         }
     }
-    if (prec == P_FP64) return run_fft_batch<MAXJ>(k_fft_inv<double, MAXJ>, jobs, n, smem, s);
-    return run_fft_batch<MAXJ>(k_fft_inv<float, MAXJ>, jobs, n, smem, s);
+    if (prec == P_FP64) return run_fft_batch<MAXJ>(k_fft_inv<double, MAXJ, NT, MB>, NT, jobs, n, smem, s);
+    return run_fft_batch<MAXJ>(k_fft_inv<float, MAXJ, NT, MB>, NT, jobs, n, smem, s);
+}
+
+template <int MAXJ>
+static st_status launch_fft_jobs_t(int dir, int prec, int variant, const FftJob *jobs, int n, size_t smem,
+                                   cudaStream_t s)
+{
+    if (prec == P_FP64 || variant == 0)
+        return launch_fft_jobs_v<MAXJ, FFT_VAR_THREADS[0], FFT_VAR_MINB[0]>(dir, prec, jobs, n, smem, s);
+    return launch_fft_jobs_v<MAXJ, FFT_VAR_THREADS[1], FFT_VAR_MINB[1]>(dir, prec, jobs, n, smem, s);
 }
 
 // dir 0: inverse (Fourier buffer -> grid), 1: direct (grid -> operand).  All
 // jobs share the precision `prec`; smem is the largest any job needs.
-st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s)
+st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s, int variant)
 {
     if (n <= 0) return ST_OK;
-    if (n == 1) return launch_fft_jobs_t<1>(dir, prec, jobs, n, smem, s);
+    if (variant < 0 || variant >= FFT_VARIANTS) return ST_ERR_ARG;
+    if (n == 1) return launch_fft_jobs_t<1>(dir, prec, variant, jobs, n, smem, s);
     if (n > MAX_JOBS) return ST_ERR_ARG;
-    return launch_fft_jobs_t<MAX_JOBS>(dir, prec, jobs, n, smem, s);
+    return launch_fft_jobs_t<MAX_JOBS>(dir, prec, variant, jobs, n, smem, s);
 }
 
 st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s)
@@ -711,7 +718,7 @@ st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t
     size_t smem = 0;
     st_status r = fft_job(p, 1, nfields, grid, p->fbop, &J, &smem);
     if (r) return r;
-    return launch_fft_jobs(1, p->prec, &J, 1, smem, s);
+    return launch_fft_jobs(1, p->prec, &J, 1, smem, s, p->fft_var[1]);
 }
 
 st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb_in)
@@ -720,7 +727,7 @@ st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, co
     size_t smem = 0;
     st_status r = fft_job(p, 0, nfields, fb_in ? fb_in : p->fb, grid, &J, &smem);
     if (r) return r;
-    return launch_fft_jobs(0, p->prec, &J, 1, smem, s);
+    return launch_fft_jobs(0, p->prec, &J, 1, smem, s, p->fft_var[0]);
 }
 
 }  // namespace st

@@ -248,6 +248,11 @@ struct st_plan {
     // freed when the last plan holding it is destroyed.
     std::shared_ptr<void> core;
 
+    // launch shapes (autotuned; see st_plan_autotune), per direction [0] inverse [1] direct
+    int fft_var[2] = {0, 0};       // FFT launch variant (threads per CTA, CTAs per SM)
+    int fft_kb[2] = {100, 100};    // FFT shared-memory budget per CTA (KB): fields per CTA
+    int nt_inv = 0;                // inverse Legendre column-tile width (0: automatic)
+
     // fault injection (tests): the next tensor-core Legendre launch withholds
     // its operand copies and bounds its waits by inject_wait_ns
     int inject_withhold = 0;
@@ -296,7 +301,8 @@ const char *kernel_name(const st_plan *p, int kind);
 
 // ---- job builders and batched launchers ----
 st_status fft_job(st_plan *p, int dir, int nfields, const void *src, void *dst, FftJob *job, size_t *smem);
-st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s);
+st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s,
+                          int variant = 0);
 st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job);
 st_status launch_pack_jobs(int dir, int prec, const PackJob *jobs, int n, cudaStream_t s);
 st_status simt_job(st_plan *p, int dir, int nfields, const void *data, void *out, SimtJob *job, long long *blocks);
@@ -316,6 +322,10 @@ struct TcJob {
 st_status tc_job(st_plan *p, int dir, int nfields, void *data, void *out, TcJob *job);
 st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s, int withhold = 0,
                          unsigned long long wait_ns = 2000000000ull);
+
+// ---- autotuner support (api.cu) ----
+st_status rebuild_legendre(st_plan *p, cudaStream_t s);
+std::string tune_key(const st_plan *p, int nfields);
 
 // ---- launchers implemented in the .cu files ----
 st_status launch_tables(st_plan *p, cudaStream_t s);

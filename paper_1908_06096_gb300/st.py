@@ -37,7 +37,8 @@ class _PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("max_fields", ctypes.c_int), ("max_m", ctypes.c_int),
                 ("spec_elems", ctypes.c_size_t), ("grid_points", ctypes.c_size_t),
                 ("element_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
-                ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t)]
+                ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
+                ("launch_shape", ctypes.c_int * 5)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -60,6 +61,7 @@ SIGNATURES = {
     "st_plan_destroy": [_VP],
     "st_plan_create_shared": [ctypes.POINTER(_VP), _VP, _I, _VP],
     "st_plan_inject": [_VP, _I, ctypes.c_uint],
+    "st_plan_autotune": [_VP, _I, ctypes.c_char_p, _VP],
     "st_plan_query": [_VP, ctypes.POINTER(_PlanInfo)],
     "st_plan_row_lengths": [_VP, ctypes.POINTER(ctypes.c_int)],
     "st_plan_nodes": [_VP, _D, _D],
@@ -247,6 +249,18 @@ class Plan:
             out = torch.empty((nf, self.nspec, 2), dtype=self.dtype, device=grid.device)
         _check(load().st_dir_trans(self._h, _ptr(grid), _ptr(out), nf, _stream_handle(stream)), "st_dir_trans")
         return out
+
+    def autotune(self, nfields: int | None = None, cache_path: str | None = None, stream=None):
+        """Time candidate launch shapes on this plan and keep the fastest
+        (st_plan_autotune); optionally append the choice to cache_path."""
+        nf = self.max_fields if nfields is None else nfields
+        _check(load().st_plan_autotune(self._h, nf, cache_path.encode() if cache_path else None,
+                                       _stream_handle(stream)), "st_plan_autotune")
+
+    def launch_shape(self):
+        info = _PlanInfo()
+        _check(load().st_plan_query(self._h, ctypes.byref(info)), "st_plan_query")
+        return list(info.launch_shape)
 
     def set_timing(self, enable: bool):
         _check(load().st_plan_set_timing(self._h, 1 if enable else 0), "st_plan_set_timing")

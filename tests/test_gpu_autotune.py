@@ -1,0 +1,45 @@
+"""Autotuner: the tuned plan still matches the oracle, the choice lands in the
+cache file, and a new plan with the same key picks it up at creation."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1908_06096_gb300 import inputs
+from tests.conftest import per_field_max_rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_autotune_keeps_results_and_caches(st_mod, oracle_mod, tmp_path, monkeypatch):
+    T, nf = 95, 24
+    cache = str(tmp_path / "tune.txt")
+    p = st_mod.Plan(T, "octahedral", precision="bf16x3", max_fields=nf)
+    p.autotune(nf, cache_path=cache)
+    shape = p.launch_shape()
+    assert shape[4] in (64, 96, 128, 160, 192, 224, 256)
+    a = inputs.spectra(T, nf, seed=31)
+    g = p.inv(torch.from_numpy(a).to("cuda", torch.float32))
+    nlat = 2 * (T + 1)
+    rows = oracle_mod.grid_rows("octahedral", nlat)
+    mu, w = oracle_mod.gauss(nlat)
+    g_ref = oracle_mod.inv_trans(T, rows, mu, a)
+    assert per_field_max_rel(g.double().cpu().numpy(), g_ref) < 2e-5
+    s = p.dir(torch.from_numpy(g_ref).to("cuda", torch.float32))
+    p.sync()
+    s_ref = oracle_mod.dir_trans(T, rows, mu, w, torch.from_numpy(g_ref).float().double().numpy())
+    s = s.double().cpu().numpy()
+    assert per_field_max_rel(s[..., 0] + 1j * s[..., 1], s_ref) < 2e-5
+    p.close()
+    assert os.path.exists(cache) and open(cache).read().strip()
+    monkeypatch.setenv("ST_TUNE_CACHE", cache)
+    q = st_mod.Plan(T, "octahedral", precision="bf16x3", max_fields=nf)
+    assert q.launch_shape() == shape
+    q.close()
