@@ -433,6 +433,7 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     for (int j = 0; j < J; ++j) {
         RowPair &rp = p->rowpairs_h[j];
         memset(&rp, 0, sizeof(rp));
+        rp.j = j;
         rp.N = p->rows[j];
         rp.M = p->Mrow[j];
         int radN[MAX_RADICES];
@@ -476,8 +477,18 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     if ((r = dmalloc(p, &p->srow, sizeof(long long) * p->srow_h.size()))) return r;
     ST_CUDA(cudaMemcpyAsync(p->srow, p->srow_h.data(), sizeof(long long) * p->srow_h.size(), cudaMemcpyHostToDevice,
                             s));
+    // device copy ordered by padded FFT length, longest first (the FFT
+    // launches take rows with equal fields-per-CTA as consecutive runs)
+    p->row_order.resize(J);
+    for (int j = 0; j < J; ++j) p->row_order[j] = j;
+    std::stable_sort(p->row_order.begin(), p->row_order.end(), [&](int a, int b) {
+        const RowPair &x = p->rowpairs_h[a], &y = p->rowpairs_h[b];
+        return fft_swz_size(x.fftlen, x.swz) > fft_swz_size(y.fftlen, y.swz);
+    });
+    std::vector<RowPair> sorted(J);
+    for (int q = 0; q < J; ++q) sorted[q] = p->rowpairs_h[p->row_order[q]];
     if ((r = dmalloc(p, &p->rowpairs, sizeof(RowPair) * J))) return r;
-    ST_CUDA(cudaMemcpyAsync(p->rowpairs, p->rowpairs_h.data(), sizeof(RowPair) * J, cudaMemcpyHostToDevice, s));
+    ST_CUDA(cudaMemcpyAsync(p->rowpairs, sorted.data(), sizeof(RowPair) * J, cudaMemcpyHostToDevice, s));
     const size_t cs = p->prec == P_FP64 ? 16 : 8;
     if ((r = dmalloc(p, &p->tw, cs * (size_t)tw))) return r;
     if ((r = launch_twiddles(p, s))) return r;
@@ -688,7 +699,7 @@ st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, 
     p->sm_count = base->sm_count; p->rows = base->rows; p->Mrow = base->Mrow; p->j0 = base->j0;
     p->npts = base->npts; p->nspec = base->nspec; p->srow_h = base->srow_h; p->srow = base->srow;
     p->srow_total = base->srow_total; p->mu = base->mu; p->w = base->w; p->rowpairs = base->rowpairs;
-    p->rowpairs_h = base->rowpairs_h; p->tw = base->tw; p->ntw = base->ntw; p->chirp = base->chirp;
+    p->rowpairs_h = base->rowpairs_h; p->row_order = base->row_order; p->tw = base->tw; p->ntw = base->ntw; p->chirp = base->chirp;
     p->kern = base->kern; p->nchirp = base->nchirp; p->nkern = base->nkern; p->max_row = base->max_row;
     p->max_fft = base->max_fft; p->max_chirp = base->max_chirp; p->max_fft_smem = base->max_fft_smem;
     p->fft_var[0] = base->fft_var[0]; p->fft_var[1] = base->fft_var[1];

@@ -29,6 +29,13 @@ struct st_batch {
 
 namespace {
 
+long long fft_ctas(const std::vector<FftJob> &jobs)
+{
+    long long n = 0;
+    for (const FftJob &J : jobs) n += (long long)J.J * J.nfg;
+    return n;
+}
+
 template <class J, class F>
 st_status chunked(const std::vector<J> &v, F f)
 {
@@ -122,20 +129,22 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n)
                 S.simt_inv.push_back(sj);
                 S.simt_inv_blocks.push_back(blocks);
             }
-            FftJob fj;
+            std::vector<FftJob> fj;
             size_t smem = 0;
-            if ((r = fft_job(p, 0, it.nfields, p->fb, it.grid, &fj, &smem))) { delete b; return r; }
-            S.fft_inv.push_back(fj);
+            if ((r = fft_jobs(p, 0, it.nfields, p->fb, it.grid, fj, &smem))) { delete b; return r; }
+            S.fft_inv.insert(S.fft_inv.end(), fj.begin(), fj.end());
             S.smem_inv = std::max(S.smem_inv, smem);
-            if ((long long)fj.J * fj.nfg > S.big_inv) { S.big_inv = (long long)fj.J * fj.nfg; S.var_inv = p->fft_var[0]; }
+            const long long ctas = fft_ctas(fj);
+            if (ctas > S.big_inv) { S.big_inv = ctas; S.var_inv = p->fft_var[0]; }
         }
         if (it.direction != 0) {
-            FftJob fj;
+            std::vector<FftJob> fj;
             size_t smem = 0;
-            if ((r = fft_job(p, 1, it.nfields, it.grid, p->fbop, &fj, &smem))) { delete b; return r; }
-            S.fft_dir.push_back(fj);
+            if ((r = fft_jobs(p, 1, it.nfields, it.grid, p->fbop, fj, &smem))) { delete b; return r; }
+            S.fft_dir.insert(S.fft_dir.end(), fj.begin(), fj.end());
             S.smem_dir = std::max(S.smem_dir, smem);
-            if ((long long)fj.J * fj.nfg > S.big_dir) { S.big_dir = (long long)fj.J * fj.nfg; S.var_dir = p->fft_var[1]; }
+            const long long ctas = fft_ctas(fj);
+            if (ctas > S.big_dir) { S.big_dir = ctas; S.var_dir = p->fft_var[1]; }
             if (prec_is_tc(p->prec)) {
                 TcJob tj;
                 if ((r = tc_job(p, 1, it.nfields, p->fbop, p->sout, &tj))) { delete b; return r; }

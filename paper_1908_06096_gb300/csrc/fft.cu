@@ -167,6 +167,37 @@ struct FastDiv {
     }
 };
 
+// Roots of unity W_L^n of one row for the passes.  With a shared-memory
+// table, W^n = T1[n / 128] T2[n % 128] (T1[a] = W^(128 a), T2[b] = W^b, both
+// copied from the row's global table at CTA start; one extra rounding); rows
+// longer than TW_SPLIT^2 read the global table.
+constexpr int TW_SPLIT = 128;
+template <typename C> struct Tw {
+    const C *g;  // W_L^n, n < L (global)
+    const C *s;  // T1 at s[0, 128), T2 at s[128, 256) (shared), or null
+    __device__ inline C operator()(int n) const
+    {
+        if (s) return cmul(s[n >> 7], s[TW_SPLIT + (n & (TW_SPLIT - 1))]);
+        return __ldg(&g[n]);
+    }
+};
+
+template <typename C>
+__device__ inline Tw<C> make_tw(const C *g, int L, C *sbuf)
+{
+    Tw<C> t;
+    t.g = g;
+    t.s = nullptr;
+    if (L <= TW_SPLIT * TW_SPLIT) {
+        for (int i = threadIdx.x; i < 2 * TW_SPLIT; i += blockDim.x) {
+            const int n = i < TW_SPLIT ? i * TW_SPLIT : i - TW_SPLIT;
+            if (n < L) sbuf[i] = __ldg(&g[n]);
+        }
+        t.s = sbuf;
+    }
+    return t;
+}
+
 // v[q] *= w^q, q = 1 .. R-1
 template <int R, typename C> __device__ inline void twiddle_powers(C *v, C w)
 {
@@ -179,13 +210,13 @@ template <int R, typename C> __device__ inline void twiddle_powers(C *v, C w)
 }
 
 template <int Ra, int Rb, bool DIT, typename C, class SW>
-__device__ inline void pass2(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, SW sw,
+__device__ inline void pass2(C *x, const Tw<C> tw, int L, int S, int Ns, int G, SW sw,
                              const C *__restrict__ kern)
 {
     const int ma = Ns / Ra, mb = ma / Rb;
     const int per = L / (Ra * Rb);
     const int sa = L / Ns, sb = L / ma;
-    const C c = __ldg(&tw[mb * sa]);  // e^{-2 pi i / (Ra Rb)}
+    const C c = tw(mb * sa);  // e^{-2 pi i / (Ra Rb)}
     const FastDiv dper(per), dmb(mb);
     for (int idx = threadIdx.x; idx < G * per; idx += blockDim.x) {
         const int f = dper(idx), t = idx - f * per;
@@ -197,8 +228,8 @@ __device__ inline void pass2(C *x, const C *__restrict__ tw, int L, int S, int N
         for (int ra = 0; ra < Ra; ++ra)
 #pragma unroll
             for (int rb = 0; rb < Rb; ++rb) v[ra][rb] = xf[sw(i0 + ra * ma + rb * mb)];
-        const C wa0 = __ldg(&tw[n1 * sa]);
-        const C wb = __ldg(&tw[n1 * sb]);
+        const C wa0 = tw(n1 * sa);
+        const C wb = tw(n1 * sb);
         if (!DIT) {
             C wa = wa0;
 #pragma unroll
@@ -253,7 +284,7 @@ __device__ inline void pass2(C *x, const C *__restrict__ tw, int L, int S, int N
 }
 
 template <int R, bool DIT, typename C, class SW>
-__device__ inline void pass1(C *x, const C *__restrict__ tw, int L, int S, int Ns, int G, SW sw,
+__device__ inline void pass1(C *x, const Tw<C> tw, int L, int S, int Ns, int G, SW sw,
                              const C *__restrict__ kern)
 {
     const int m = Ns / R;
@@ -268,7 +299,7 @@ __device__ inline void pass1(C *x, const C *__restrict__ tw, int L, int S, int N
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = xf[sw(i0 + r * m)];
-        const C w = __ldg(&tw[n1 * sa]);
+        const C w = tw(n1 * sa);
         if (!DIT) {
             dftR<R>(v);
             twiddle_powers<R>(v, w);
@@ -286,7 +317,7 @@ __device__ inline void pass1(C *x, const C *__restrict__ tw, int L, int S, int N
 }
 
 template <bool DIT, typename C, class SW>
-__device__ inline void run_pass2(int Ra, int Rb, C *x, const C *tw, int L, int S, int Ns, int G, SW sw,
+__device__ inline void run_pass2(int Ra, int Rb, C *x, const Tw<C> tw, int L, int S, int Ns, int G, SW sw,
                                  const C *kern)
 {
 #define ST_P2(A, B) \
@@ -297,7 +328,7 @@ __device__ inline void run_pass2(int Ra, int Rb, C *x, const C *tw, int L, int S
 }
 
 template <bool DIT, typename C, class SW>
-__device__ inline void run_pass1(int R, C *x, const C *tw, int L, int S, int Ns, int G, SW sw, const C *kern)
+__device__ inline void run_pass1(int R, C *x, const Tw<C> tw, int L, int S, int Ns, int G, SW sw, const C *kern)
 {
     if (R == 2) pass1<2, DIT, C, SW>(x, tw, L, S, Ns, G, sw, kern);
     else if (R == 3) pass1<3, DIT, C, SW>(x, tw, L, S, Ns, G, sw, kern);
@@ -308,11 +339,14 @@ __device__ inline void run_pass1(int R, C *x, const C *tw, int L, int S, int Ns,
 // Stages are fused in pairs when the pair holds at most 16 points (the
 // register budget); fusing or not does not change the result.
 constexpr int MAX_FUSED = 16;
+// Items per thread per round in the load and store loops (independent global
+// loads in flight before the first use).
+constexpr int FFT_U = 4;
 
 // All DIF stages over rp.rad (natural -> digit-reversed).  With `kern`, the
 // last pass also multiplies by the kernel spectrum and conjugates.
 template <typename C, class SW>
-__device__ void fft_dif(C *x, const C *tw, const RowPair &rp, int G, int S, const C *kern)
+__device__ void fft_dif(C *x, const Tw<C> tw, const RowPair &rp, int G, int S, const C *kern)
 {
     const int L = rp.fftlen;
     const SW sw;
@@ -335,7 +369,7 @@ __device__ void fft_dif(C *x, const C *tw, const RowPair &rp, int G, int S, cons
 
 // All DIT stages (digit-reversed -> natural): the stages in reverse order.
 template <typename C, class SW>
-__device__ void fft_dit(C *x, const C *tw, const RowPair &rp, int G, int S)
+__device__ void fft_dit(C *x, const Tw<C> tw, const RowPair &rp, int G, int S)
 {
     const int L = rp.fftlen;
     const SW sw;
@@ -358,7 +392,7 @@ __device__ void fft_dit(C *x, const C *tw, const RowPair &rp, int G, int S)
 // order; mode 1: premultiplied by the chirp and zero up to L).  Afterwards
 // fft_value(m) gives Z_m.
 template <typename C, class SW>
-__device__ inline void fft_forward(C *x, const C *tw, const C *__restrict__ kern, const RowPair &rp, int G, int S)
+__device__ inline void fft_forward(C *x, const Tw<C> tw, const C *__restrict__ kern, const RowPair &rp, int G, int S)
 {
     fft_dif<C, SW>(x, tw, rp, G, S, rp.mode == 1 ? kern : nullptr);
     if (rp.mode == 1) fft_dit<C, SW>(x, tw, rp, G, S);
@@ -437,7 +471,7 @@ __device__ inline void load_rowpair(RowPair *dst, const RowPair *src)
 }
 
 template <typename Rr, int S, class SW>
-__device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, int f0)
+__device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, int f0, void *tws)
 {
     typedef typename CT<Rr>::T C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -448,38 +482,63 @@ __device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, i
     const Rr *grid = (const Rr *)J.src;
     void *fb = J.dst;
     C *x = (C *)smem_raw;
-    const C *tw = (const C *)J.tw + rp.tw_off;
+    const Tw<C> tw = make_tw<C>((const C *)J.tw + rp.tw_off, W, (C *)tws);
     const C *chirp = (const C *)J.chirp + rp.chirp_off;
     const SW sw;
 
-    for (int f = 0; f < G; ++f) {
-        const int fld = f0 + f;
-        const Rr *g = grid + (long long)fld * npts;
-        for (int k = threadIdx.x; k < W; k += blockDim.x) {
-            C v;
-            v.x = 0;
-            v.y = 0;
-            if (fld < nfields && k < N) {
-                v.x = g[rp.off_n + k];
-                v.y = g[rp.off_s + k];
-                if (rp.mode == 1) v = cmul(v, __ldg(&chirp[k]));
+    // FFT_U items per thread per round, all loads issued before any use
+    const FastDiv dW(W);
+    const int nt = blockDim.x;
+    for (int base = threadIdx.x; base < G * W; base += FFT_U * nt) {
+        C v[FFT_U], c[FFT_U];
+        int pos[FFT_U];
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            const int idx = base + u * nt;
+            const int f = dW(idx), k = idx - f * W;
+            const int fld = f0 + f;
+            pos[u] = idx < G * W ? f * SL + sw(k) : -1;
+            v[u].x = 0;
+            v[u].y = 0;
+            c[u].x = 1;
+            c[u].y = 0;
+            if (idx < G * W && fld < nfields && k < N) {
+                const Rr *g = grid + (long long)fld * npts;
+                v[u].x = g[rp.off_n + k];
+                v[u].y = g[rp.off_s + k];
+                if (rp.mode == 1) c[u] = __ldg(&chirp[k]);
             }
-            x[(size_t)f * SL + sw(k)] = v;
         }
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u)
+            if (pos[u] >= 0) x[pos[u]] = rp.mode == 1 ? cmul(v[u], c[u]) : v[u];
     }
     __syncthreads();
-    fft_forward<C, SW>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, SL);
+    // slots past the last field hold zeros and need no transform
+    fft_forward<C, SW>(x, tw, (const C *)J.kern + rp.kern_off, rp, min(G, nfields - f0), SL);
 
     const Rr inv = (Rr)1.0 / (Rr)N;
     const int M = rp.M;
     const FastDiv dG(G);
-    for (int idx = threadIdx.x; idx < (M + 1) * G; idx += blockDim.x) {
+    for (int base = threadIdx.x; base < (M + 1) * G; base += FFT_U * nt) {
+    C zmu[FFT_U], zcu[FFT_U];
+#pragma unroll
+    for (int u = 0; u < FFT_U; ++u) {
+        const int idx = min(base + u * nt, (M + 1) * G - 1);
+        const int m = dG(idx), f = idx - m * G;
+        const C *xf = x + (size_t)f * SL;
+        zmu[u] = fft_value<C, SW>(xf, chirp, rp, m);
+        zcu[u] = fft_value<C, SW>(xf, chirp, rp, m == 0 ? 0 : N - m);
+    }
+#pragma unroll
+    for (int u = 0; u < FFT_U; ++u) {
+        const int idx = base + u * nt;
+        if (idx >= (M + 1) * G) break;
         const int m = dG(idx), f = idx - m * G;
         const int fld = f0 + f;
         if (fld >= nfields) continue;
-        const C *xf = x + (size_t)f * SL;
-        C zm = fft_value<C, SW>(xf, chirp, rp, m);
-        C zc = cconj(m == 0 ? zm : fft_value<C, SW>(xf, chirp, rp, N - m));
+        const C zm = zmu[u];
+        const C zc = cconj(zcu[u]);
         // north spectrum A = (zm + zc)/2, south spectrum B = -i (zm - zc)/2
         Rr ax = (zm.x + zc.x) * (Rr)0.5, ay = (zm.y + zc.y) * (Rr)0.5;
         Rr dx = (zm.x - zc.x) * (Rr)0.5, dy = (zm.y - zc.y) * (Rr)0.5;
@@ -491,28 +550,31 @@ __device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, i
         store_pair<S, Rr>(fb, rE, 2 * fld, Cp, Rp, plane_stride, ex, ey);
         store_pair<S, Rr>(fb, rO, 2 * fld, Cp, Rp, plane_stride, ox, oy);
     }
+    }
 }
 
 template <typename Rr, int S, int MAXJ, int NT, int MB>
 __global__ void __launch_bounds__(NT, (FftBounds<Rr, MB>::MINB)) k_fft_dir(const __grid_constant__ FftBatch<MAXJ> B)
 {
     __shared__ RowPair rp;
+    __shared__ __align__(16) typename CT<Rr>::T tws[2 * TW_SPLIT];
     const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
     const FftJob &J = B.job[q];
     const int b = (int)(blockIdx.x - B.prefix[q]);
-    const int j = b / J.nfg;
-    const int f0 = (b - j * J.nfg) * J.G;
-    load_rowpair(&rp, J.rps + j);
+    const int rr = b / J.nfg;
+    const int f0 = (b - rr * J.nfg) * J.G;
+    load_rowpair(&rp, J.rps + J.r0 + rr);
+    const int j = rp.j;
     switch (rp.swz) {
-    case 1: fft_dir_body<Rr, S, Swz<1>>(J, rp, j, f0); break;
-    case 2: fft_dir_body<Rr, S, Swz<2>>(J, rp, j, f0); break;
-    case 3: fft_dir_body<Rr, S, Swz<3>>(J, rp, j, f0); break;
-    default: fft_dir_body<Rr, S, Swz<0>>(J, rp, j, f0); break;
+    case 1: fft_dir_body<Rr, S, Swz<1>>(J, rp, j, f0, tws); break;
+    case 2: fft_dir_body<Rr, S, Swz<2>>(J, rp, j, f0, tws); break;
+    case 3: fft_dir_body<Rr, S, Swz<3>>(J, rp, j, f0, tws); break;
+    default: fft_dir_body<Rr, S, Swz<0>>(J, rp, j, f0, tws); break;
     }
 }
 
 template <typename Rr, class SW>
-__device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, int f0)
+__device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, int f0, void *tws)
 {
     typedef typename CT<Rr>::T C;
     typedef typename CT<Rr>::T C2;
@@ -524,7 +586,7 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
     const Rr *fb = (const Rr *)J.src;
     Rr *grid = (Rr *)J.dst;
     C *x = (C *)smem_raw;
-    const C *tw = (const C *)J.tw + rp.tw_off;
+    const Tw<C> tw = make_tw<C>((const C *)J.tw + rp.tw_off, rp.fftlen, (C *)tws);
     const C *chirp = (const C *)J.chirp + rp.chirp_off;
     const SW sw;
 
@@ -539,54 +601,81 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
     // times the chirp at the same place for Bluestein rows
     const int M = rp.M;
     const FastDiv dG(G);
-    for (int idx = threadIdx.x; idx < (M + 1) * G; idx += blockDim.x) {
-        const int m = dG(idx), f = idx - m * G;
-        const int fld = f0 + f;
-        if (fld >= nfields) continue;
-        const long long rS = ((long long)m * Jp + j) * Cp + 2 * fld;
-        const long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * fld;
-        // the odd-parity half of m = T is empty (no n = T + 1), so its rows are
-        // never written by the Legendre stage: A = 0 there
-        const C2 sv = *(const C2 *)(fb + rS);
-        C2 av;
-        av.x = 0;
-        av.y = 0;
-        if (m < T) av = *(const C2 *)(fb + rA);
-        const Rr sx = sv.x, sy = sv.y, axx = av.x, ayy = av.y;
-        const Rr nx = sx + axx, ny = sy + ayy;  // north F_m
-        const Rr qx = sx - axx, qy = sy - ayy;  // south F_m
-        C *xf = x + (size_t)f * S;
-        if (m == 0) {
-            C v;
-            v.x = nx;
-            v.y = -qx;
-            if (rp.mode == 1) v = cmul(v, __ldg(&chirp[0]));
-            xf[sw(0)] = v;
-        } else {
-            C a, bb;
-            a.x = nx - qy;
-            a.y = -(ny + qx);
-            bb.x = nx + qy;
-            bb.y = ny - qx;
-            if (rp.mode == 1) {
-                a = cmul(a, __ldg(&chirp[m]));
-                bb = cmul(bb, __ldg(&chirp[N - m]));
+    const int nt = blockDim.x;
+    for (int base = threadIdx.x; base < (M + 1) * G; base += FFT_U * nt) {
+        C2 sv[FFT_U], av[FFT_U];
+        C ca[FFT_U], cb[FFT_U];
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            const int idx = base + u * nt;
+            const int m = dG(idx), f = idx - m * G;
+            const int fld = f0 + f;
+            sv[u].x = sv[u].y = av[u].x = av[u].y = 0;
+            ca[u].x = cb[u].x = 1;
+            ca[u].y = cb[u].y = 0;
+            if (idx < (M + 1) * G && fld < nfields) {
+                const long long rS = ((long long)m * Jp + j) * Cp + 2 * fld;
+                const long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * fld;
+                sv[u] = *(const C2 *)(fb + rS);
+                // the odd-parity half of m = T is empty (no n = T + 1), so its
+                // rows are never written by the Legendre stage: A = 0 there
+                if (m < T) av[u] = *(const C2 *)(fb + rA);
+                if (rp.mode == 1) {
+                    ca[u] = __ldg(&chirp[m]);
+                    cb[u] = __ldg(&chirp[m == 0 ? 0 : N - m]);
+                }
             }
-            xf[sw(m)] = a;
-            xf[sw(N - m)] = bb;
+        }
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            const int idx = base + u * nt;
+            const int m = dG(idx), f = idx - m * G;
+            if (idx >= (M + 1) * G || f0 + f >= nfields) continue;
+            const Rr sx = sv[u].x, sy = sv[u].y, axx = av[u].x, ayy = av[u].y;
+            const Rr nx = sx + axx, ny = sy + ayy;  // north F_m
+            const Rr qx = sx - axx, qy = sy - ayy;  // south F_m
+            C *xf = x + (size_t)f * S;
+            if (m == 0) {
+                C v;
+                v.x = nx;
+                v.y = -qx;
+                if (rp.mode == 1) v = cmul(v, ca[u]);
+                xf[sw(0)] = v;
+            } else {
+                C a, bb;
+                a.x = nx - qy;
+                a.y = -(ny + qx);
+                bb.x = nx + qy;
+                bb.y = ny - qx;
+                if (rp.mode == 1) {
+                    a = cmul(a, ca[u]);
+                    bb = cmul(bb, cb[u]);
+                }
+                xf[sw(m)] = a;
+                xf[sw(N - m)] = bb;
+            }
         }
     }
     __syncthreads();
-    fft_forward<C, SW>(x, tw, (const C *)J.kern + rp.kern_off, rp, G, S);
-    for (int f = 0; f < G; ++f) {
-        const int fld = f0 + f;
-        if (fld >= nfields) break;
-        Rr *g = grid + (long long)fld * npts;
-        const C *xf = x + (size_t)f * S;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) {
-            const C v = fft_value<C, SW>(xf, chirp, rp, k);
-            g[rp.off_n + k] = v.x;
-            g[rp.off_s + k] = -v.y;
+    const int Gv = min(G, nfields - f0);
+    fft_forward<C, SW>(x, tw, (const C *)J.kern + rp.kern_off, rp, Gv, S);
+    const FastDiv dN(N);
+    for (int base = threadIdx.x; base < Gv * N; base += FFT_U * nt) {
+        C v[FFT_U];
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            const int idx = min(base + u * nt, Gv * N - 1);
+            const int f = dN(idx), k = idx - f * N;
+            v[u] = fft_value<C, SW>(x + (size_t)f * S, chirp, rp, k);
+        }
+#pragma unroll
+        for (int u = 0; u < FFT_U; ++u) {
+            const int idx = base + u * nt;
+            if (idx >= Gv * N) break;
+            const int f = dN(idx), k = idx - f * N;
+            Rr *g = grid + (long long)(f0 + f) * npts;
+            g[rp.off_n + k] = v[u].x;
+            g[rp.off_s + k] = -v[u].y;
         }
     }
 }
@@ -595,35 +684,37 @@ template <typename Rr, int MAXJ, int NT, int MB>
 __global__ void __launch_bounds__(NT, (FftBounds<Rr, MB>::MINB)) k_fft_inv(const __grid_constant__ FftBatch<MAXJ> B)
 {
     __shared__ RowPair rp;
+    __shared__ __align__(16) typename CT<Rr>::T tws[2 * TW_SPLIT];
     const int q = find_job<MAXJ>(B.prefix, B.njobs, blockIdx.x);
     const FftJob &J = B.job[q];
     const int b = (int)(blockIdx.x - B.prefix[q]);
-    const int j = b / J.nfg;
-    const int f0 = (b - j * J.nfg) * J.G;
-    load_rowpair(&rp, J.rps + j);
+    const int rr = b / J.nfg;
+    const int f0 = (b - rr * J.nfg) * J.G;
+    load_rowpair(&rp, J.rps + J.r0 + rr);
+    const int j = rp.j;
     switch (rp.swz) {
-    case 1: fft_inv_body<Rr, Swz<1>>(J, rp, j, f0); break;
-    case 2: fft_inv_body<Rr, Swz<2>>(J, rp, j, f0); break;
-    case 3: fft_inv_body<Rr, Swz<3>>(J, rp, j, f0); break;
-    default: fft_inv_body<Rr, Swz<0>>(J, rp, j, f0); break;
+    case 1: fft_inv_body<Rr, Swz<1>>(J, rp, j, f0, tws); break;
+    case 2: fft_inv_body<Rr, Swz<2>>(J, rp, j, f0, tws); break;
+    case 3: fft_inv_body<Rr, Swz<3>>(J, rp, j, f0, tws); break;
+    default: fft_inv_body<Rr, Swz<0>>(J, rp, j, f0, tws); break;
     }
 }
 
-// Fields per CTA: one shared-memory buffer of fftlen complex values each,
-// within the plan's per-CTA budget for this direction (autotuned).
-static int fft_fields_per_cta(const st_plan *p, int dir, int nfields, size_t *smem)
+// Fields per CTA.  A CTA transforms G fields of one row pair, one shared-
+// memory slot of the row's padded FFT length each, within the plan's per-CTA
+// budget for this direction (autotuned).  G is the largest power of two (at
+// most FFT_MAX_G and nfields) whose slots fit, so short rows near the poles
+// take many fields per CTA and long rows few.
+constexpr int FFT_MAX_G = 64;
+
+static int fft_fields_for_slot(const st_plan *p, int dir, int nfields, int slot)
 {
     const size_t cs = p->prec == P_FP64 ? 16 : 8;
-    const size_t per = (size_t)p->max_fft_smem * cs;
     const size_t budget = p->prec == P_FP64 ? 110 * 1024 : (size_t)p->fft_kb[dir] * 1024;
-    int G = (int)(budget / per);
-    if (G < 1) G = 1;
-    if (G > 8) G = 8;
-    if (G > nfields) G = nfields;
-    *smem = per * (size_t)G;
-    return G;
+    int G = 1;
+    while (G < FFT_MAX_G && G < nfields && (size_t)(2 * G) * slot * cs <= budget) G *= 2;
+    return std::min(G, nfields);
 }
-
 template <typename K>
 static st_status set_smem(K kern, size_t smem)
 {
@@ -631,27 +722,53 @@ static st_status set_smem(K kern, size_t smem)
     return ST_OK;
 }
 
-st_status fft_job(st_plan *p, int dir, int nfields, const void *src, void *dst, FftJob *job, size_t *smem)
+// The jobs of one FFT launch over all row pairs of `p` for `nfields` fields.
+// The plan's device row-pair array is ordered by padded FFT length, longest
+// first, so the rows that share one G form consecutive runs (G only grows
+// along the array) and the longest CTAs start first; one job per run, its
+// slot the longest padded length in the run.  *smem is the most any job needs.
+st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst, std::vector<FftJob> &jobs,
+                   size_t *smem)
 {
-    FftJob &J = *job;
-    J.rps = p->rowpairs;
-    J.tw = p->tw;
-    J.chirp = p->chirp;
-    J.kern = p->kern;
-    J.src = src;
-    J.dst = dst;
-    J.npts = p->npts;
-    J.nfields = nfields;
-    J.G = fft_fields_per_cta(p, dir, nfields, smem);
-    J.Sslot = p->max_fft_smem;
-    J.Cp = cols_padded(nfields);
-    J.Rp = fb_rows(p);
-    J.ps = J.Rp * J.Cp;
-    J.T = p->T;
-    J.Jp = p->Jp;
-    J.J = p->J;
-    J.nfg = (nfields + J.G - 1) / J.G;
-    if (*smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
+    const size_t cs = p->prec == P_FP64 ? 16 : 8;
+    const int J = p->J;
+    std::vector<int> slot(J), G(J);
+    for (int r = 0; r < J; ++r) {
+        const RowPair &rp = p->rowpairs_h[p->row_order[r]];
+        slot[r] = fft_swz_size(rp.fftlen, rp.swz);
+        G[r] = fft_fields_for_slot(p, dir, nfields, slot[r]);
+    }
+    FftJob base;
+    memset(&base, 0, sizeof(base));
+    base.rps = p->rowpairs;
+    base.tw = p->tw;
+    base.chirp = p->chirp;
+    base.kern = p->kern;
+    base.src = src;
+    base.dst = dst;
+    base.npts = p->npts;
+    base.nfields = nfields;
+    base.Cp = cols_padded(nfields);
+    base.Rp = fb_rows(p);
+    base.ps = base.Rp * base.Cp;
+    base.T = p->T;
+    base.Jp = p->Jp;
+    size_t need = 0;
+    for (int r = 0; r < J;) {
+        int e = r + 1;
+        while (e < J && G[e] == G[r]) ++e;
+        FftJob J1 = base;
+        J1.r0 = r;
+        J1.J = e - r;
+        J1.G = G[r];
+        J1.Sslot = *std::max_element(slot.begin() + r, slot.begin() + e);
+        J1.nfg = (nfields + J1.G - 1) / J1.G;
+        need = std::max(need, (size_t)J1.G * J1.Sslot * cs);
+        jobs.push_back(J1);
+        r = e;
+    }
+    *smem = std::max(*smem, need);
+    if (need > 227 * 1024) return ST_ERR_UNSUPPORTED;
     return ST_OK;
 }
 
@@ -714,20 +831,20 @@ st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t s
 
 st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s)
 {
-    FftJob J;
+    std::vector<FftJob> jobs;
     size_t smem = 0;
-    st_status r = fft_job(p, 1, nfields, grid, p->fbop, &J, &smem);
+    st_status r = fft_jobs(p, 1, nfields, grid, p->fbop, jobs, &smem);
     if (r) return r;
-    return launch_fft_jobs(1, p->prec, &J, 1, smem, s, p->fft_var[1]);
+    return launch_fft_jobs(1, p->prec, jobs.data(), (int)jobs.size(), smem, s, p->fft_var[1]);
 }
 
 st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb_in)
 {
-    FftJob J;
+    std::vector<FftJob> jobs;
     size_t smem = 0;
-    st_status r = fft_job(p, 0, nfields, fb_in ? fb_in : p->fb, grid, &J, &smem);
+    st_status r = fft_jobs(p, 0, nfields, fb_in ? fb_in : p->fb, grid, jobs, &smem);
     if (r) return r;
-    return launch_fft_jobs(0, p->prec, &J, 1, smem, s, p->fft_var[0]);
+    return launch_fft_jobs(0, p->prec, jobs.data(), (int)jobs.size(), smem, s, p->fft_var[0]);
 }
 
 }  // namespace st

@@ -67,6 +67,7 @@ struct RowPair {
     long long kern_off;       // mode 1: L values FFT_L(b) / L, b the conjugate chirp wrapped circularly
     long long off_n;          // offset of the northern row inside one field's grid
     long long off_s;          // offset of the southern row
+    int j;                    // row pair index (0 = nearest the north pole)
 };
 
 // One Legendre GEMM: zonal wavenumber m, parity p (n - m even: 0, odd: 1),
@@ -104,6 +105,9 @@ __host__ __device__ inline int fft_swz(int i, int mode)
 }
 __host__ __device__ inline int fft_swz_size(int L, int mode)
 {
+    // mode 3 permutes within aligned blocks of 16, so a partial last block
+    // reaches up to the next multiple of 16
+    if (mode == 3) return (L + 15) & ~15;
     return mode == 1 ? L + (L >> 4) + 1 : (mode == 2 ? L + (L >> 5) + 1 : L);
 }
 
@@ -149,7 +153,8 @@ struct FftJob {
     const void *src;          // direct: grid; inverse: Fourier buffer (S, A)
     void *dst;                // direct: Fourier-buffer operand (E, O); inverse: grid
     long long npts, Rp, ps;
-    int nfields, G, Sslot, Cp, T, Jp, J, nfg;
+    int nfields, G, Sslot, Cp, T, Jp, nfg;
+    int r0, J;                // entries r0 .. r0 + J - 1 of the plan's row-pair array
 };
 template <int MAXJ>
 struct FftBatch {
@@ -210,7 +215,9 @@ struct st_plan {
 
     // FFT data
     st::RowPair *rowpairs = nullptr;     // device, J entries
-    std::vector<st::RowPair> rowpairs_h;
+    std::vector<st::RowPair> rowpairs_h;  // by row index j
+    std::vector<int> row_order;           // device array entry r holds row row_order[r]
+                                          // (longest padded FFT first)
     void *tw = nullptr;                  // device roots of unity (double2 or float2)
     long long ntw = 0;
     void *chirp = nullptr;               // Bluestein chirps (double2 or float2)
@@ -300,7 +307,8 @@ enum KernelKind {
 const char *kernel_name(const st_plan *p, int kind);
 
 // ---- job builders and batched launchers ----
-st_status fft_job(st_plan *p, int dir, int nfields, const void *src, void *dst, FftJob *job, size_t *smem);
+st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst, std::vector<FftJob> &jobs,
+                   size_t *smem);
 st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s,
                           int variant = 0);
 st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job);
