@@ -424,7 +424,7 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     if ((r = launch_gauss(nlat, p->mu, p->w, s))) return r;
 
     // FFT rows: mixed radix over N where N is 5-smooth, otherwise Bluestein
-    // over a 5-smooth L >= 2N - 1
+    // over a 5-smooth L >= N + 2M
     p->rowpairs_h.resize(J);
     long long off = 0, tw = 0, nch = 0, nkn = 0;
     std::vector<long long> roff(nlat);
@@ -441,7 +441,10 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
         long long prod = 1;
         for (int q = 0; q < nN; ++q) prod *= radN[q];
         if (prod != rp.N) return ST_ERR_UNSUPPORTED;
-        const int L = smooth_at_least(2 * rp.N - 1);
+        // Bluestein length: the circular convolution must hold N + 2M
+        // consecutive chirp offsets (inputs at 2M + 1 wavenumbers and N
+        // outputs, or the reverse), so L >= N + 2M
+        const int L = smooth_at_least(rp.N + 2 * rp.M);
         int radL[MAX_RADICES];
         int nL = factorize(L, radL);
         pair_radices(radN, nN);
@@ -494,7 +497,7 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     if ((r = launch_twiddles(p, s))) return r;
     if (nch > 0) {
         if ((r = dmalloc(p, &p->chirp, cs * (size_t)nch))) return r;
-        if ((r = dmalloc(p, &p->kern, cs * (size_t)nkn))) return r;
+        if ((r = dmalloc(p, &p->kern, cs * 2 * (size_t)nkn))) return r;  // direct, then inverse
         if ((r = launch_bluestein_setup(p, s))) return r;
     }
 

@@ -406,6 +406,16 @@ __device__ inline C fft_value(const C *xf, const C *__restrict__ chirp, const Ro
     return cmul(__ldg(&chirp[m]), cconj(xf[sw(m)]));
 }
 
+// Z_{-m} (= Z_{N-m}), 1 <= m <= M.  Bluestein rows hold offset -m at L - m,
+// and w_{-m} = w_m.
+template <typename C, class SW>
+__device__ inline C fft_value_neg(const C *xf, const C *__restrict__ chirp, const RowPair &rp, int m)
+{
+    const SW sw;
+    if (rp.mode == 0) return xf[sw(dif_pos(rp.N - m, rp))];
+    return cmul(__ldg(&chirp[m]), cconj(xf[sw(rp.fftlen - m)]));
+}
+
 __device__ inline float round_tf32_f(float x)
 {
     uint32_t r;
@@ -528,7 +538,7 @@ __device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, i
         const int m = dG(idx), f = idx - m * G;
         const C *xf = x + (size_t)f * SL;
         zmu[u] = fft_value<C, SW>(xf, chirp, rp, m);
-        zcu[u] = fft_value<C, SW>(xf, chirp, rp, m == 0 ? 0 : N - m);
+        zcu[u] = m == 0 ? zmu[u] : fft_value_neg<C, SW>(xf, chirp, rp, m);
     }
 #pragma unroll
     for (int u = 0; u < FFT_U; ++u) {
@@ -621,8 +631,8 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
                 // rows are never written by the Legendre stage: A = 0 there
                 if (m < T) av[u] = *(const C2 *)(fb + rA);
                 if (rp.mode == 1) {
-                    ca[u] = __ldg(&chirp[m]);
-                    cb[u] = __ldg(&chirp[m == 0 ? 0 : N - m]);
+                    ca[u] = __ldg(&chirp[m]);  // w_{-m} = w_m
+                    cb[u] = ca[u];
                 }
             }
         }
@@ -652,7 +662,8 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
                     bb = cmul(bb, cb[u]);
                 }
                 xf[sw(m)] = a;
-                xf[sw(N - m)] = bb;
+                // wavenumber -m: at N - m for the N-point FFT, at L - m for Bluestein
+                xf[sw(rp.mode == 1 ? rp.fftlen - m : N - m)] = bb;
             }
         }
     }
@@ -743,7 +754,8 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
     base.rps = p->rowpairs;
     base.tw = p->tw;
     base.chirp = p->chirp;
-    base.kern = p->kern;
+    // the inverse's Bluestein kernel spectra follow all rows' direct ones
+    base.kern = (const char *)p->kern + (dir == 0 ? cs * (size_t)p->nkern : 0);
     base.src = src;
     base.dst = dst;
     base.npts = p->npts;

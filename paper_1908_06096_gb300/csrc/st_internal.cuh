@@ -64,7 +64,9 @@ struct RowPair {
     int swz;                  // shared-memory address map (see fft_swz)
     long long tw_off;         // first of the row's fftlen roots of unity e^{-2 pi i t / fftlen}
     long long chirp_off;      // mode 1: N chirp values w_k = e^{-i pi k^2 / N}
-    long long kern_off;       // mode 1: L values FFT_L(b) / L, b the conjugate chirp wrapped circularly
+    long long kern_off;       // mode 1: L values FFT_L(b) / L, b the conjugate chirp over the row's
+                              // offsets wrapped circularly (direct; the inverse's mirror image
+                              // follows all rows' direct spectra)
     long long off_n;          // offset of the northern row inside one field's grid
     long long off_s;          // offset of the southern row
     int j;                    // row pair index (0 = nearest the north pole)

@@ -237,11 +237,15 @@ __global__ void k_twiddles(const RowPair *rp, int J, C *tw)
 // Bluestein's identity m k = (m^2 + k^2 - (m - k)^2) / 2 turns the N-point DFT
 //   Z_m = sum_k z_k e^{-2 pi i m k / N}
 // into Z_m = w_m sum_k (z_k w_k) conj(w_{m-k}) with the chirp
-// w_k = e^{-i pi k^2 / N}: a convolution, done circularly at any length
-// L >= 2N - 1 with the conjugate chirp b wrapped around (b_i = conj(w_i) for
-// 0 <= i < N, b_{L-d} = conj(w_d) for 1 <= d < N, zero between).  The plan
-// keeps w and FFT_L(b) / L; both are computed here in FP64 (k^2 reduced
-// mod 2N exactly in integers before the angle is formed).
+// w_k = e^{-i pi k^2 / N}, for every integer m: a convolution with the
+// conjugate chirp b_d = conj(w_d) over the offsets d = m - k that occur, done
+// circularly at a length L that holds them all.
+//   direct:  inputs k in [0, N), outputs m in [-M, M]  -> d in [-(N-1+M), M]
+//   inverse: inputs m in [-M, M], outputs k in [0, N)  -> d in [-M, N-1+M]
+// so L >= N + 2M and each direction's b is the other's mirror image
+// (b_inv[i] = b_dir[-i mod L], hence FFT(b_inv)[k] = FFT(b_dir)[-k mod L]).
+// The plan keeps w and both FFT_L(b) / L; all computed here in FP64 (k^2
+// reduced mod 2N exactly in integers before the angle is formed).
 
 __device__ inline void chirp_val(long long k, int N, double &c, double &s)
 {
@@ -282,9 +286,9 @@ __global__ void k_bluestein_kern(const RowPair *rps, int J, double2 *scratch, lo
     double2 *x = scratch + r.kern_off, *y = scratch + nkern + r.kern_off;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         double2 v = make_double2(0.0, 0.0);
-        long long d = -1;
-        if (i < N) d = i;
-        else if (i > L - N) d = L - i;
+        long long d = -1;  // direct offsets: [0, M] at i = d, [-(N-1+M), -1] at i = L + d
+        if (i <= r.M) d = i;
+        else if (i >= L - (N - 1 + r.M)) d = L - i;
         if (d >= 0) {
             double c, s;
             chirp_val(d, N, c, s);
@@ -322,10 +326,14 @@ __global__ void k_bluestein_kern(const RowPair *rps, int J, double2 *scratch, lo
     // output in, so the pointwise product needs no permutation
     const double inv = 1.0 / (double)L;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const double2 vd = x[i], vi = x[i == 0 ? 0 : L - i];
         C v;
-        v.x = (decltype(v.x))(x[i].x * inv);
-        v.y = (decltype(v.y))(x[i].y * inv);
+        v.x = (decltype(v.x))(vd.x * inv);
+        v.y = (decltype(v.y))(vd.y * inv);
         kern[r.kern_off + dif_pos(i, r)] = v;
+        v.x = (decltype(v.x))(vi.x * inv);
+        v.y = (decltype(v.y))(vi.y * inv);
+        kern[nkern + r.kern_off + dif_pos(i, r)] = v;
     }
 }
 
