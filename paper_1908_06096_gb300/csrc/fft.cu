@@ -468,6 +468,17 @@ __device__ inline void store_pair(void *base, long long r, int c, int Cp, long l
     }
 }
 
+// FP32 grid rows whose north and south segments start at 16-byte boundaries
+// and hold whole groups of 4 points (true of the octahedral rows 20 + 4i and
+// of regular grids with nlon a multiple of 4): the grid side moves 4 points
+// per access.
+template <typename Rr>
+__device__ inline bool grid_vec4(const void *grid, const RowPair &rp, long long npts)
+{
+    if (sizeof(Rr) != 4) return false;
+    return ((rp.off_n | rp.off_s | npts | (long long)rp.N) & 3) == 0 && ((uintptr_t)grid & 15) == 0;
+}
+
 template <typename Rr, int MB> struct FftBounds { static constexpr int MINB = MB; };
 template <int MB> struct FftBounds<double, MB> { static constexpr int MINB = 1; };
 
@@ -499,6 +510,50 @@ __device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, i
     // FFT_U items per thread per round, all loads issued before any use
     const FastDiv dW(W);
     const int nt = blockDim.x;
+    if (grid_vec4<Rr>(grid, rp, npts)) {
+        // rows of 4-float multiples at 16-byte boundaries: 4 points per load
+        const int W4 = W >> 2;
+        const FastDiv dW4(W4);
+        for (int base = threadIdx.x; base < G * W4; base += 2 * nt) {
+            float4 vn[2], vs[2];
+            C c[2][4];
+            int f[2], k[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = base + u * nt;
+                f[u] = dW4(idx);
+                k[u] = 4 * (idx - f[u] * W4);
+                vn[u] = vs[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    c[u][e].x = 1;
+                    c[u][e].y = 0;
+                }
+                if (idx < G * W4 && f0 + f[u] < nfields && k[u] < N) {
+                    const float *g = (const float *)grid + (long long)(f0 + f[u]) * npts;
+                    vn[u] = __ldg((const float4 *)(g + rp.off_n + k[u]));
+                    vs[u] = __ldg((const float4 *)(g + rp.off_s + k[u]));
+                    if (rp.mode == 1) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) c[u][e] = __ldg(&chirp[k[u] + e]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (base + u * nt >= G * W4) break;
+                const float re[4] = {vn[u].x, vn[u].y, vn[u].z, vn[u].w};
+                const float im[4] = {vs[u].x, vs[u].y, vs[u].z, vs[u].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    C v;
+                    v.x = re[e];
+                    v.y = im[e];
+                    x[f[u] * SL + sw(k[u] + e)] = rp.mode == 1 ? cmul(v, c[u][e]) : v;
+                }
+            }
+        }
+    } else
     for (int base = threadIdx.x; base < G * W; base += FFT_U * nt) {
         C v[FFT_U], c[FFT_U];
         int pos[FFT_U];
@@ -670,6 +725,21 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
     __syncthreads();
     const int Gv = min(G, nfields - f0);
     fft_forward<C, SW>(x, tw, (const C *)J.kern + rp.kern_off, rp, Gv, S);
+    if (grid_vec4<Rr>(grid, rp, npts)) {
+        const int N4 = N >> 2;
+        const FastDiv dN4(N4);
+        for (int idx = threadIdx.x; idx < Gv * N4; idx += nt) {
+            const int f = dN4(idx), k = 4 * (idx - f * N4);
+            const C *xf = x + (size_t)f * S;
+            C v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = fft_value<C, SW>(xf, chirp, rp, k + e);
+            float *g = (float *)grid + (long long)(f0 + f) * npts;
+            *(float4 *)(g + rp.off_n + k) = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+            *(float4 *)(g + rp.off_s + k) = make_float4(-v[0].y, -v[1].y, -v[2].y, -v[3].y);
+        }
+        return;
+    }
     const FastDiv dN(N);
     for (int base = threadIdx.x; base < Gv * N; base += FFT_U * nt) {
         C v[FFT_U];
