@@ -182,3 +182,53 @@ def test_nfields_bounds(st_mod):
     with pytest.raises(st_mod.STError):
         p.inv(x)
     p.close()
+
+
+# Rows whose length is not a multiple of 4 take the scalar grid path of the
+# FFT kernels (the others move 4 points per access): nlon = 66 = 2 3 11 runs
+# Bluestein rows, nlon = 90 = 2 3^2 5 mixed-radix rows.
+ODD_ROWS = [
+    (31, 32, 66, "bf16x3"),
+    (31, 32, 90, "bf16x3"),
+    (31, 32, 66, "fp32"),
+    (31, 32, 90, "fp64"),
+]
+
+
+@pytest.mark.parametrize("T,nlat,nlon,prec", ODD_ROWS)
+def test_rows_not_multiple_of_four(st_mod, oracle_mod, T, nlat, nlon, prec):
+    nf = 7
+    rows = oracle_mod.grid_rows("regular", nlat, nlon)
+    mu, w = oracle_mod.gauss(nlat)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    a = inputs.spectra(T, nf, seed=2000 + nlon)
+    p = st_mod.Plan(T, "regular", nlat=nlat, nlon=nlon, precision=prec, max_fields=nf)
+    g = p.inv(_dev(a, dt))
+    g_ref = oracle_mod.inv_trans(T, rows, mu, a)
+    assert per_field_max_rel(g.double().cpu().numpy(), g_ref) < TOL[prec]
+    g_in = _dev(g_ref, dt)
+    s = p.dir(g_in)
+    p.sync()
+    s_ref = oracle_mod.dir_trans(T, rows, mu, w, g_in.double().cpu().numpy())
+    s = s.double().cpu().numpy()
+    assert per_field_max_rel(s[..., 0] + 1j * s[..., 1], s_ref) < TOL[prec]
+    p.close()
+
+
+def test_grid_pointer_off_16_byte_boundary(st_mod):
+    """A grid buffer 4 bytes past a 16-byte boundary takes the scalar path and
+    gives the same numbers as an aligned one."""
+    T, nf = 63, 9
+    p = st_mod.Plan(T, "octahedral", precision="bf16x3", max_fields=nf)
+    spec = _dev(inputs.spectra(T, nf, seed=77), torch.float32)
+    g_al = p.inv(spec).clone()
+    flat = torch.zeros(nf * p.npts + 4, dtype=torch.float32, device="cuda")
+    g_off = flat[1:1 + nf * p.npts].view(nf, p.npts)
+    assert g_off.data_ptr() % 16 == 4
+    p.inv(spec, out=g_off)
+    s_al = p.dir(g_al).clone()
+    s_off = p.dir(g_off).clone()
+    torch.cuda.synchronize()
+    assert max_rel(g_off.cpu().numpy(), g_al.cpu().numpy()) <= 1e-6
+    assert max_rel(s_off.cpu().numpy(), s_al.cpu().numpy()) <= 1e-6
+    p.close()
