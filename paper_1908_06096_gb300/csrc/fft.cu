@@ -479,6 +479,32 @@ __device__ inline bool grid_vec4(const void *grid, const RowPair &rp, long long 
     return ((rp.off_n | rp.off_s | npts | (long long)rp.N) & 3) == 0 && ((uintptr_t)grid & 15) == 0;
 }
 
+// Four consecutive values (two fields' re, im) of one row-major row starting
+// at element idx, a multiple of 4: one 16-byte store (FP32) or one 8-byte
+// store per plane (BF16 hi/lo).
+template <int S, typename Rr>
+__device__ inline void store_quad(void *base, long long idx, long long ps, const Rr *v)
+{
+    if (S == S_F32) {
+        *(float4 *)((float *)base + idx) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    } else if (S == S_BF16_SPLIT) {
+        __nv_bfloat162 hi[2], lo[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float a = (float)v[2 * h], b = (float)v[2 * h + 1];
+            hi[h] = __floats2bfloat162_rn(a, b);
+            lo[h] = __floats2bfloat162_rn(a - __low2float(hi[h]), b - __high2float(hi[h]));
+        }
+        uint2 uh, ul;
+        uh.x = *(const unsigned *)&hi[0];
+        uh.y = *(const unsigned *)&hi[1];
+        ul.x = *(const unsigned *)&lo[0];
+        ul.y = *(const unsigned *)&lo[1];
+        *(uint2 *)((__nv_bfloat16 *)base + idx) = uh;
+        *(uint2 *)((__nv_bfloat16 *)base + idx + ps) = ul;
+    }
+}
+
 template <typename Rr, int MB> struct FftBounds { static constexpr int MINB = MB; };
 template <int MB> struct FftBounds<double, MB> { static constexpr int MINB = 1; };
 
@@ -584,6 +610,51 @@ __device__ inline void fft_dir_body(const FftJob &J, const RowPair &rp, int j, i
 
     const Rr inv = (Rr)1.0 / (Rr)N;
     const int M = rp.M;
+    if ((S == S_BF16_SPLIT || S == S_F32) && (G & 1) == 0) {
+        // two adjacent fields per item: their (re, im) columns are adjacent,
+        // so E and O each take one 4-column store per plane; one chirp value
+        // serves both fields and both signs of m (w_{-m} = w_m)
+        const int G2 = G >> 1;
+        const FastDiv dG2(G2);
+        for (int idx = threadIdx.x; idx < (M + 1) * G2; idx += nt) {
+            const int m = dG2(idx), f = 2 * (idx - m * G2);
+            const int fld = f0 + f;
+            if (fld >= nfields) continue;
+            C cm;
+            cm.x = 1;
+            cm.y = 0;
+            if (rp.mode == 1) cm = __ldg(&chirp[m]);
+            Rr e4[4], o4[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const C *xf = x + (size_t)(f + h) * SL;
+                C zm, zc;
+                if (rp.mode == 1) {
+                    zm = cmul(cm, cconj(xf[sw(m)]));
+                    zc = m == 0 ? zm : cmul(cm, cconj(xf[sw(rp.fftlen - m)]));
+                } else {
+                    zm = xf[sw(dif_pos(m, rp))];
+                    zc = m == 0 ? zm : xf[sw(dif_pos(N - m, rp))];
+                }
+                zc = cconj(zc);
+                Rr ax = (zm.x + zc.x) * (Rr)0.5, ay = (zm.y + zc.y) * (Rr)0.5;
+                Rr dx = (zm.x - zc.x) * (Rr)0.5, dy = (zm.y - zc.y) * (Rr)0.5;
+                Rr bx = dy, by = -dx;
+                Rr ex = (ax + bx) * inv, ey = (ay + by) * inv;
+                Rr ox = (ax - bx) * inv, oy = (ay - by) * inv;
+                if (m == 0) { ey = 0; oy = 0; }
+                if (fld + h >= nfields) { ex = ey = ox = oy = 0; }  // padding columns stay zero
+                e4[2 * h] = ex;
+                e4[2 * h + 1] = ey;
+                o4[2 * h] = ox;
+                o4[2 * h + 1] = oy;
+            }
+            const long long rE = (long long)m * Jp + j, rO = ((long long)(T + 1) + m) * Jp + j;
+            store_quad<S, Rr>(fb, rE * Cp + 2 * fld, plane_stride, e4);
+            store_quad<S, Rr>(fb, rO * Cp + 2 * fld, plane_stride, o4);
+        }
+        return;
+    }
     const FastDiv dG(G);
     for (int base = threadIdx.x; base < (M + 1) * G; base += FFT_U * nt) {
     C zmu[FFT_U], zcu[FFT_U];
@@ -665,8 +736,67 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
     // conj(Z): Z[m] = Xn + i Xs, Z[N-m] = conj(Xn) + i conj(Xs), Z[0] = Re Xn + i Re Xs,
     // times the chirp at the same place for Bluestein rows
     const int M = rp.M;
-    const FastDiv dG(G);
     const int nt = blockDim.x;
+    if (sizeof(Rr) == 4 && (G & 1) == 0) {
+        // two adjacent fields per item: one 16-byte load each of S and A (the
+        // column pair of an odd last field is padding, read but not used)
+        const int G2 = G >> 1;
+        const FastDiv dG2(G2);
+        for (int base = threadIdx.x; base < (M + 1) * G2; base += 2 * nt) {
+            float4 sv[2], av[2];
+            C cw[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = base + u * nt;
+                const int m = dG2(idx), fld = f0 + 2 * (idx - m * G2);
+                sv[u] = av[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cw[u].x = 1;
+                cw[u].y = 0;
+                if (idx < (M + 1) * G2 && fld < nfields) {
+                    const long long rS = ((long long)m * Jp + j) * Cp + 2 * fld;
+                    const long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * fld;
+                    sv[u] = *(const float4 *)((const float *)fb + rS);
+                    if (m < T) av[u] = *(const float4 *)((const float *)fb + rA);
+                    if (rp.mode == 1) cw[u] = __ldg(&chirp[m]);  // w_{-m} = w_m
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = base + u * nt;
+                if (idx >= (M + 1) * G2) break;
+                const int m = dG2(idx), f = 2 * (idx - m * G2);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (f0 + f + h >= nfields) break;
+                    const Rr sx = h ? sv[u].z : sv[u].x, sy = h ? sv[u].w : sv[u].y;
+                    const Rr axx = h ? av[u].z : av[u].x, ayy = h ? av[u].w : av[u].y;
+                    const Rr nx = sx + axx, ny = sy + ayy;  // north F_m
+                    const Rr qx = sx - axx, qy = sy - ayy;  // south F_m
+                    C *xf = x + (size_t)(f + h) * S;
+                    if (m == 0) {
+                        C v;
+                        v.x = nx;
+                        v.y = -qx;
+                        if (rp.mode == 1) v = cmul(v, cw[u]);
+                        xf[sw(0)] = v;
+                    } else {
+                        C a, bb;
+                        a.x = nx - qy;
+                        a.y = -(ny + qx);
+                        bb.x = nx + qy;
+                        bb.y = ny - qx;
+                        if (rp.mode == 1) {
+                            a = cmul(a, cw[u]);
+                            bb = cmul(bb, cw[u]);
+                        }
+                        xf[sw(m)] = a;
+                        xf[sw(rp.mode == 1 ? rp.fftlen - m : N - m)] = bb;
+                    }
+                }
+            }
+        }
+    } else {
+    const FastDiv dG(G);
     for (int base = threadIdx.x; base < (M + 1) * G; base += FFT_U * nt) {
         C2 sv[FFT_U], av[FFT_U];
         C ca[FFT_U], cb[FFT_U];
@@ -721,6 +851,7 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
                 xf[sw(rp.mode == 1 ? rp.fftlen - m : N - m)] = bb;
             }
         }
+    }
     }
     __syncthreads();
     const int Gv = min(G, nfields - f0);
