@@ -8,14 +8,17 @@
 // sequence z = north + i south, so a single complex FFT of length N serves
 // both.  Every transform runs in place in shared memory (one buffer per
 // field) as mixed-radix passes over radices 2, 3, 4, 5; each pass fuses two
-// radix stages in registers (a 16-point pass for 4 x 4), so a 5184-point FFT
-// takes 4 trips through shared memory.  Roots of unity, chirps and kernel
-// spectra are read through the read-only cache.
+// radix stages in registers (a 16-point pass for 4 x 4), so a 3888-point FFT
+// takes 4 trips through shared memory.  Roots of unity come from a two-level
+// table in shared memory; chirps and kernel spectra are read through the
+// read-only cache.  The plan stores the rows longest first and gives each
+// run of rows its own number of fields per CTA (G).
 //
 //  mode 0 (N 5-smooth): decimation-in-frequency passes; the output sits in
 //          digit-reversed order and is read through the index map pos(m).
 //  mode 1 (Bluestein): the N-point DFT as a chirp-weighted circular
-//          convolution of length L >= 2N - 1:
+//          convolution of length L >= N + 2M (2M + 1 wavenumbers on one
+//          side, N points on the other):
 //              Z_m = w_m sum_k (z_k w_k) conj(w_{m-k}),  w_k = e^{-i pi k^2 / N}
 //          done as DIF (natural -> digit-reversed), a pointwise product with
 //          the kernel spectrum stored in that same digit-reversed order, and

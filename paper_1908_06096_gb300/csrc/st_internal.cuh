@@ -52,7 +52,7 @@ constexpr int MAX_RADICES = 24;
 // nlat-1-j; both have N points.
 //  mode 0: the N-point DFT runs as Stockham passes over the radices of N.
 //  mode 1: Bluestein: the N-point DFT is a chirp-weighted circular
-//          convolution of length fftlen = L >= 2N - 1 (L 5-smooth), done with
+//          convolution of length fftlen = L >= N + 2M (L 5-smooth), done with
 //          two L-point Stockham FFTs and a precomputed kernel spectrum.
 struct RowPair {
     int N;                    // points per row
