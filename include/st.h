@@ -123,12 +123,11 @@ st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int pr
 st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, void *stream);
 
 /*
- * Autotuner (not in the paper; SURVEY-level "per-m tile shapes picked by an
- * autotuner").  Times, on this plan and for `nfields` fields, candidate FFT
- * launch shapes (threads per CTA, CTAs per SM, fields per CTA) for each
- * direction and, on tensor-core plans, candidate column-tile widths of the
- * inverse per-m Legendre GEMMs (re-laying out the tables), and keeps the
- * fastest.  Synchronous; allocates a temporary grid buffer.  If cache_path is
+ * Autotuner (not in the paper).  Times, on this plan and for `nfields`
+ * fields, candidate FFT launch shapes (fields per CTA, through the per-CTA
+ * shared-memory budget) for each direction and, on tensor-core plans,
+ * candidate column-tile widths of the per-m Legendre GEMMs (re-laying out the
+ * tables), and keeps the fastest.  Synchronous; allocates a temporary grid buffer.  If cache_path is
  * not NULL the choice is appended to that text file; st_plan_create applies a
  * matching entry (same T, grid, precision, field-count bucket and SM count)
  * from the file named by the ST_TUNE_CACHE environment variable.
@@ -255,6 +254,16 @@ st_status st_plan_set_timing(st_plan_t plan, int enable);
  * Synchronises on the recorded events. */
 st_status st_plan_timings(st_plan_t plan, st_kernel_time *out, int max, int *n);
 st_status st_plan_reset_timings(st_plan_t plan);
+
+/*
+ * Deployment check (not in the paper): the compute capability of the current
+ * device and the architecture the library's kernels were compiled for, as
+ * the CUDA runtime reports it for a kernel of this library
+ * (cudaFuncAttributes::binaryVersion: 103 for sm_103a code).  Any pointer
+ * may be NULL.  ST_ERR_CUDA when there is no usable device or the kernels
+ * cannot run on it.
+ */
+st_status st_build_info(int *cc_major, int *cc_minor, int *binary_version);
 
 /* Text for a status code (static storage). */
 const char *st_status_string(st_status s);

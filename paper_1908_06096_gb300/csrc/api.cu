@@ -449,7 +449,38 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
         int nL = factorize(L, radL);
         pair_radices(radN, nN);
         pair_radices(radL, nL);
-        if (!smooth5(radN, nN)) {
+        rp.fast = -1;
+        // FP32 plans: a compile-time plan of length N, else Bluestein on the
+        // shortest compile-time plan of length >= N + 2M; the generic kernel
+        // only for what neither covers (and for FP64)
+        int fid = -1, fL = 0;
+        bool fblue = false;
+        if (p->prec != P_FP64) {
+            for (int id = 0; id < FF_NPLANS && fid < 0; ++id)
+                if (ff_length(id) == rp.N) fid = id;
+            if (fid < 0) {
+                for (int id = 0; id < FF_NPLANS; ++id) {
+                    const int Lf = ff_length(id);
+                    if (Lf >= rp.N + 2 * rp.M && (fid < 0 || Lf < fL)) { fid = id; fL = Lf; }
+                }
+                fblue = fid >= 0;
+            }
+            if (fid >= 0) fL = ff_length(fid);
+        }
+        if (fid >= 0) {
+            rp.fast = fid;
+            rp.mode = fblue ? 1 : 0;
+            rp.fftlen = fL;
+            rp.nrad = ff_radices(fid, rp.rad);
+            rp.swz = 0;
+            if (fblue) {
+                rp.chirp_off = nch;
+                rp.kern_off = nkn;
+                nch += rp.N;
+                nkn += fL;
+                p->max_chirp = std::max(p->max_chirp, rp.N);
+            }
+        } else if (!smooth5(radN, nN)) {
             rp.mode = 1;
             rp.fftlen = L;
             rp.nrad = nL;
@@ -465,7 +496,7 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
             rp.nrad = nN;
             memcpy(rp.rad, radN, sizeof(int) * nN);
         }
-        rp.swz = pick_swizzle(rp.fftlen, rp.rad, rp.nrad);
+        if (rp.fast < 0) rp.swz = pick_swizzle(rp.fftlen, rp.rad, rp.nrad);
         p->max_fft_smem = std::max(p->max_fft_smem, fft_swz_size(rp.fftlen, rp.swz));
         rp.tw_off = tw;
         tw += rp.fftlen;
@@ -484,10 +515,16 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
     // launches take rows with equal fields-per-CTA as consecutive runs)
     p->row_order.resize(J);
     for (int j = 0; j < J; ++j) p->row_order[j] = j;
+    // (fast rows first, by plan length, longest first)
     std::stable_sort(p->row_order.begin(), p->row_order.end(), [&](int a, int b) {
         const RowPair &x = p->rowpairs_h[a], &y = p->rowpairs_h[b];
+        const bool fx = x.fast >= 0, fy = y.fast >= 0;
+        if (fx != fy) return fx;
+        if (fx) return x.fftlen > y.fftlen;
         return fft_swz_size(x.fftlen, x.swz) > fft_swz_size(y.fftlen, y.swz);
     });
+    p->nfast = 0;
+    for (int j = 0; j < J; ++j) p->nfast += p->rowpairs_h[j].fast >= 0;
     std::vector<RowPair> sorted(J);
     for (int q = 0; q < J; ++q) sorted[q] = p->rowpairs_h[p->row_order[q]];
     if ((r = dmalloc(p, &p->rowpairs, sizeof(RowPair) * J))) return r;
@@ -627,11 +664,29 @@ static st_status fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t
     return counted(p, K_FFT_DIR, s, [&] { return launch_fft_dir(p, grid, nfields, s); });
 }
 
+// An empty kernel compiled like every other in the library: its attributes
+// tell st_build_info which architecture the library's code targets.
+__global__ void k_build_probe() {}
+
 }  // namespace st
 
 using namespace st;
 
 extern "C" {
+
+st_status st_build_info(int *cc_major, int *cc_minor, int *binary_version)
+{
+    int dev = 0;
+    ST_CUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    ST_CUDA(cudaGetDeviceProperties(&prop, dev));
+    cudaFuncAttributes attr;
+    ST_CUDA(cudaFuncGetAttributes(&attr, k_build_probe));
+    if (cc_major) *cc_major = prop.major;
+    if (cc_minor) *cc_minor = prop.minor;
+    if (binary_version) *binary_version = attr.binaryVersion;
+    return ST_OK;
+}
 
 const char *st_status_string(st_status s)
 {
@@ -668,6 +723,7 @@ st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int pr
     p->nlon = grid->kind == ST_GRID_REGULAR ? grid->nlon : 0;
     p->prec = prec;
     p->max_fields = max_fields;
+    if (prec != ST_FP64) p->fft_kb[0] = p->fft_kb[1] = 72;  // fast kernels: 3 CTAs per SM
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaGetDevice"); }
     cudaDeviceProp prop;
@@ -705,6 +761,7 @@ st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, 
     p->rowpairs_h = base->rowpairs_h; p->row_order = base->row_order; p->tw = base->tw; p->ntw = base->ntw; p->chirp = base->chirp;
     p->kern = base->kern; p->nchirp = base->nchirp; p->nkern = base->nkern; p->max_row = base->max_row;
     p->max_fft = base->max_fft; p->max_chirp = base->max_chirp; p->max_fft_smem = base->max_fft_smem;
+    p->nfast = base->nfast;
     p->fft_var[0] = base->fft_var[0]; p->fft_var[1] = base->fft_var[1];
     p->fft_kb[0] = base->fft_kb[0]; p->fft_kb[1] = base->fft_kb[1]; p->nt_inv = base->nt_inv;
     for (int d = 0; d < 2; ++d) {

@@ -1,0 +1,8 @@
+// Fast FP32 row FFTs, direct direction, plan group 1 (fft_fast_inst.cuh).
+// the direct runs best at 80 registers a thread (3 CTAs per SM)
+#define FF_MINB 3
+#define FF_DIR 1
+#define FF_GROUP 1
+#define FF_KERNEL k_fftf_dir_g1
+#define FF_LAUNCH launch_fftf_dir_g1
+#include "fft_fast_inst.cuh"

@@ -1,0 +1,13 @@
+// Generic row-FFT kernel instance: inverse direction, FP32.
+#include "fft_generic.cuh"
+
+namespace st {
+
+st_status launch_gen_inv_f32(const FftJob *jobs, int n, size_t smem, cudaStream_t s)
+{
+    if (n <= 0) return ST_OK;
+    if (n > MAX_JOBS) return ST_ERR_ARG;
+    return run_fft_batch<MAX_JOBS>(k_fft_inv<float, MAX_JOBS, 256, 2>, 256, jobs, n, smem, s);
+}
+
+}  // namespace st

@@ -70,7 +70,68 @@ struct RowPair {
     long long off_n;          // offset of the northern row inside one field's grid
     long long off_s;          // offset of the southern row
     int j;                    // row pair index (0 = nearest the north pole)
+    int fast;                 // compile-time FP32 plan of length fftlen (ST_FF_PLANS id), -1: generic kernel
 };
+
+// FP32 FFT plans with compile-time radices (fft_fast.cuh): id, translation-
+// unit group, radices R1 .. R4 (1 = unused), L = R1 R2 R3 R4.  Later radices
+// are 16 wherever the length allows, which keeps every pass free of shared-
+// memory bank conflicts under the pad-16 layout.
+#define ST_FF_PLANS(X)                                                                                 \
+    X(0, 0, 4, 4, 1, 1) X(1, 0, 5, 4, 1, 1) X(2, 0, 6, 4, 1, 1) X(3, 0, 2, 16, 1, 1)                      \
+    X(4, 0, 10, 4, 1, 1) X(5, 0, 3, 16, 1, 1) X(6, 0, 4, 16, 1, 1) X(7, 0, 5, 16, 1, 1)                   \
+    X(8, 0, 6, 16, 1, 1) X(9, 0, 8, 16, 1, 1) X(10, 0, 10, 16, 1, 1) X(11, 0, 12, 16, 1, 1)               \
+    X(12, 0, 16, 16, 1, 1) X(13, 1, 2, 10, 16, 1) X(14, 1, 3, 8, 16, 1) X(15, 1, 2, 16, 16, 1)            \
+    X(16, 1, 4, 10, 16, 1) X(17, 1, 3, 16, 16, 1) X(18, 1, 4, 16, 16, 1) X(19, 1, 5, 16, 16, 1)           \
+    X(20, 1, 6, 16, 16, 1) X(21, 1, 8, 16, 16, 1) X(22, 1, 10, 16, 16, 1) X(23, 1, 12, 16, 16, 1)         \
+    X(24, 1, 16, 16, 16, 1) X(25, 2, 2, 10, 16, 16) X(26, 2, 2, 12, 16, 16) X(27, 2, 2, 16, 16, 16)
+constexpr int FF_NPLANS = 28;
+constexpr int FF_NGROUPS = 3;
+// shared-memory slot of one field for a plan of length L (pad-16 layout)
+__host__ __device__ inline int ff_slot(int L) { return L + (L >> 4) + 1; }
+// host lookups into ST_FF_PLANS
+inline int ff_group(int id)
+{
+    switch (id) {
+#define X(i, g, a, b, c, d) \
+    case i: return g;
+        ST_FF_PLANS(X)
+#undef X
+    }
+    return -1;
+}
+inline int ff_radices(int id, int *rad)
+{
+    switch (id) {
+#define X(i, g, a, b, c, d)                                                  \
+    case i: {                                                                \
+        const int r_[4] = {a, b, c, d};                                      \
+        int n_ = 0;                                                          \
+        for (int k_ = 0; k_ < 4; ++k_)                                       \
+            if (r_[k_] > 1) rad[n_++] = r_[k_];                              \
+        return n_;                                                           \
+    }
+        ST_FF_PLANS(X)
+#undef X
+    }
+    return 0;
+}
+inline int ff_length(int id)
+{
+    int rad[4], L = 1;
+    const int n = ff_radices(id, rad);
+    for (int k = 0; k < n; ++k) L *= rad[k];
+    return n ? L : 0;
+}
+// Shared memory of a fast-kernel CTA beyond its field slots (FP32 complex
+// elements): the L / R1 base roots when there are at most 512 of them.
+inline int ff_table_elems(int id)
+{
+    int rad[4];
+    ff_radices(id, rad);
+    const int twn = ff_length(id) / rad[0];
+    return twn <= 512 ? twn : 0;
+}
 
 // One Legendre GEMM: zonal wavenumber m, parity p (n - m even: 0, odd: 1),
 // in one direction.  out[col][c] = sum_r tab[col][r] * data[r][c].
@@ -148,7 +209,7 @@ __device__ inline int find_job(const long long *prefix, int njobs, long long b)
     return lo;
 }
 
-// One FFT stage of one request.
+// One FFT stage of one request over a run of rows that share a launch shape.
 struct FftJob {
     const RowPair *rps;
     const void *tw, *chirp, *kern;
@@ -157,6 +218,10 @@ struct FftJob {
     long long npts, Rp, ps;
     int nfields, G, Sslot, Cp, T, Jp, nfg;
     int r0, J;                // entries r0 .. r0 + J - 1 of the plan's row-pair array
+    int kind;                 // -1: generic kernel; else the fast kernel group of `plan`
+    int plan;                 // fast plan id (ST_FF_PLANS)
+    int smode;                // storage mode of the direct output (fast kernels)
+    int smem;                 // dynamic shared memory one CTA of this job needs (bytes)
 };
 template <int MAXJ>
 struct FftBatch {
@@ -229,6 +294,7 @@ struct st_plan {
     int max_fft = 0;                     // largest fftlen
     int max_fft_smem = 0;                // largest shared-memory slot (fftlen after padding)
     int max_chirp = 0;                   // largest N among Bluestein rows
+    int nfast = 0;                       // rows on the fast kernels: entries 0 .. nfast-1 of rowpairs
 
     // Legendre data, [0] inverse, [1] direct
     void *tab[2] = {nullptr, nullptr};
@@ -313,6 +379,14 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
                    size_t *smem);
 st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s,
                           int variant = 0);
+// fast-kernel launch of n jobs of one group (all jobs' kind == group), one direction
+st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_dir_g0(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_dir_g1(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_dir_g2(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_inv_g0(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_inv_g1(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_inv_g2(const FftJob *jobs, int n, cudaStream_t s);
 st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job);
 st_status launch_pack_jobs(int dir, int prec, const PackJob *jobs, int n, cudaStream_t s);
 st_status simt_job(st_plan *p, int dir, int nfields, const void *data, void *out, SimtJob *job, long long *blocks);

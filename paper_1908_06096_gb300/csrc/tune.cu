@@ -1,7 +1,7 @@
 // Autotuner (st_plan_autotune): times candidate launch shapes on the plan
 // itself and keeps the fastest.
-//  - FFT, per direction: launch variant (threads per CTA, CTAs per SM) and
-//    the shared-memory budget per CTA, which sets how many fields a CTA holds.
+//  - FFT, per direction: the shared-memory budget per CTA, which sets how
+//    many fields a CTA holds (FP32 plans).
 //  - Tensor-core Legendre: the inverse column-tile width (the tile shape of
 //    the per-m GEMMs; changing it re-lays out the tables).
 // The choice can be appended to a cache file; st_plan_create applies a
@@ -49,8 +49,9 @@ extern "C" st_status st_plan_autotune(st_plan_t p, int nfields, const char *cach
     const int reps = 3;
 
     // FFT launch shapes, per direction
-    const int kbs[] = {40, 56, 100, 150, 200};
-    const int nvar = p->prec == P_FP64 ? 1 : 2;
+    // (FP64 plans size their CTAs by a fixed budget: nothing to choose)
+    const int kbs[] = {36, 54, 72, 108, 144};
+    const int nvar = p->prec == P_FP64 ? 0 : 1;
     for (int dir = 0; dir < 2 && r == ST_OK; ++dir) {
         float best = 1e30f;
         int bv = p->fft_var[dir], bk = p->fft_kb[dir];

@@ -85,6 +85,7 @@ SIGNATURES = {
     "st_batch_run": [_VP, _VP, _I],
     "st_batch_destroy": [_VP],
     "st_static_scratch_bytes": [],
+    "st_build_info": [ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
 }
 
 
@@ -127,6 +128,13 @@ def _stream_handle(stream) -> int:
 
 def _ptr(t: torch.Tensor) -> int:
     return int(t.data_ptr())
+
+
+def build_info():
+    """(compute capability major, minor, kernel binary version) from st_build_info."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().st_build_info(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "st_build_info")
+    return a.value, b.value, c.value
 
 
 def gauss_nodes(nlat: int, stream=None):

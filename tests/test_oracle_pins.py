@@ -275,3 +275,30 @@ def test_inverse_is_linear_and_fields_are_independent(oracle_mod):
     assert np.array_equal(g[1:2], g1)
     g_sum = oracle_mod.inv_trans(T, rows, mu, a[0:1] + 2 * a[2:3])
     assert np.max(np.abs(g_sum - (g[0:1] + 2 * g[2:3]))) < 1e-13
+
+
+# ---------------------------------------------------------------- grid geometry
+
+def test_octahedral_grid_rule(oracle_mod):
+    """Row i from either pole (i = 1 .. nlat/2) of the octahedral grid has
+    20 + 4 i points (the configuration's O640 grid: 1280 latitudes, 24 points
+    on the polar rows, 2580 on the two equatorial rows, 1 666 560 in all),
+    mirrored about the equator."""
+    rows = oracle_mod.grid_rows("octahedral", 1280)
+    assert rows.shape == (1280,)
+    assert rows[0] == rows[-1] == 24
+    assert rows[639] == rows[640] == 2580
+    assert int(rows.sum()) == 1_666_560
+    for j in range(640):
+        assert rows[j] == 20 + 4 * (j + 1) == rows[1279 - j], j
+    # O1280 (2560 latitudes): 20 + 4 i up to 5140 points at the equator
+    big = oracle_mod.grid_rows("octahedral", 2560)
+    assert big[0] == 24 and big[1279] == big[1280] == 5140
+    assert int(big.sum()) == 2 * sum(20 + 4 * i for i in range(1, 1281))
+
+
+def test_regular_grid_rule(oracle_mod):
+    rows = oracle_mod.grid_rows("regular", 160, 320)
+    assert rows.shape == (160,) and np.all(rows == 320)
+    with pytest.raises(RuntimeError):
+        oracle_mod.grid_rows("regular", 31, 64)      # odd number of latitudes
