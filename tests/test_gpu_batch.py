@@ -1,6 +1,14 @@
-"""Batched execution (st_batch_*): every request's result inside a mixed
-batch of truncations, grids and precisions is the same as the request run
-alone (within the split-precision tolerance), with and without graph replay."""
+"""Batched execution (st_batch_*).
+
+Every request of a mixed batch of truncations, grids and precisions is
+compared with the FP64 oracle (the synthesis and analysis definitions), with
+and without graph replay, and with the same request run alone.  A second case
+runs requests of the mixed-truncation configuration's sizes (T639 on O640
+with 220 fields in BF16x3, T511 on the regular 512 x 1024 grid with 200
+fields in 3xTF32) in one batch, sampled fields against the oracle.
+
+Bars: 1e-12 (FP64), 2e-5 (FP32, 3xTF32, BF16x3) normwise per field.
+"""
 import numpy as np
 import pytest
 import torch
@@ -28,6 +36,10 @@ REQS = [
 ]
 
 
+def _tol(prec):
+    return 1e-12 if prec == "fp64" else 2e-5
+
+
 def _make(st_mod, idx, T, grid, prec, nf, direction):
     p = st_mod.Plan(T, grid, precision=prec, max_fields=nf)
     spec = torch.from_numpy(inputs.spectra(T, nf, seed=500 + idx)).to("cuda", p.dtype)
@@ -38,8 +50,44 @@ def _make(st_mod, idx, T, grid, prec, nf, direction):
     return p, spec, g, out
 
 
+class _Oracle:
+    """Oracle results of one plan's geometry (nodes, rows) on host arrays."""
+
+    def __init__(self, oracle_mod, plan):
+        self.o = oracle_mod
+        self.T = plan.T
+        self.rows = oracle_mod.grid_rows(plan.grid, plan.nlat, plan.nlon)
+        self.mu, self.w = oracle_mod.gauss(plan.nlat)
+
+    def inv(self, spec):
+        return self.o.inv_trans(self.T, self.rows, self.mu, spec)
+
+    def dir(self, grid):
+        return self.o.dir_trans(self.T, self.rows, self.mu, self.w, grid)
+
+
+def _cplx(s):
+    s = np.asarray(s, dtype=np.float64)
+    return s[..., 0] + 1j * s[..., 1]
+
+
+def _check_vs_oracle(orc, prec, spec, grid_in, grid_out, spec_out, direction, pick=None):
+    """Compare a request's outputs (host arrays) with the oracle on fields `pick`."""
+    pick = list(range(len(spec))) if pick is None else list(pick)
+    tol = _tol(prec)
+    if direction in ("inv", "round"):
+        ref = orc.inv(spec[pick])
+        err = per_field_max_rel(grid_out[pick], ref)
+        assert err < tol, ("inverse", err)
+    if direction in ("dir", "round"):
+        src = grid_out if direction == "round" else grid_in
+        ref = orc.dir(src[pick])
+        err = per_field_max_rel(_cplx(spec_out[pick]), ref)
+        assert err < tol, ("direct", err)
+
+
 @pytest.mark.parametrize("graph", [False, True])
-def test_batch_matches_individual_calls(st_mod, graph):
+def test_batch_matches_oracle_and_individual_calls(st_mod, oracle_mod, graph):
     setups = [_make(st_mod, i, *r) for i, r in enumerate(REQS)]
     refs = []
     for (p, spec, g, out), r in zip(setups, REQS):
@@ -63,14 +111,55 @@ def test_batch_matches_individual_calls(st_mod, graph):
         batch.run(graph=graph)
         torch.cuda.synchronize()
         for (p, spec, g, out), r, (gref, sref) in zip(setups, REQS, refs):
-            tol = 1e-12 if r[2] == "fp64" else 2e-5
+            prec, d = r[2], r[4]
+            gh = g.double().cpu().numpy()
+            sh = out.double().cpu().numpy()
+            # against the oracle
+            _check_vs_oracle(_Oracle(oracle_mod, p), prec, spec.double().cpu().numpy(), gh, gh, sh, d)
+            # and against the same request run alone on the GPU
+            tol = _tol(prec)
             if gref is not None:
-                assert per_field_max_rel(g.double().cpu().numpy(), gref.double().cpu().numpy()) <= tol, r
+                assert per_field_max_rel(gh, gref.double().cpu().numpy()) <= tol, r
             if sref is not None:
-                assert per_field_max_rel(out.double().cpu().numpy(), sref.double().cpu().numpy()) <= tol, r
+                assert per_field_max_rel(sh, sref.double().cpu().numpy()) <= tol, r
     batch.close()
     for p, *_ in setups:
         p.sync()
+        p.close()
+
+
+def test_batch_at_mixed_truncation_sizes_vs_oracle(st_mod, oracle_mod):
+    """Requests of the mixed-truncation configuration's largest sizes in one
+    graph-replayed batch; fields 0 and the last of each against the oracle."""
+    cases = [
+        # T, grid, nlat, nlon, precision, nfields, seed
+        (639, "octahedral", 1280, 0, "bf16x3", 220, 1103),
+        (511, "regular", 512, 1024, "tf32x3", 200, 1104),
+        (159, "octahedral", 320, 0, "bf16x3", 37, 1105),
+    ]
+    setups = []
+    for T, grid, nlat, nlon, prec, nf, seed in cases:
+        p = st_mod.Plan(T, grid, nlat=nlat, nlon=nlon or None, precision=prec, max_fields=nf)
+        a = inputs.spectra(T, nf, seed=seed)
+        spec = torch.from_numpy(a).to("cuda", p.dtype)
+        g = torch.zeros((nf, p.npts), dtype=p.dtype, device="cuda")
+        out = torch.zeros((nf, p.nspec, 2), dtype=p.dtype, device="cuda")
+        setups.append((p, a, spec, g, out, prec, nf))
+    batch = st_mod.Batch([(p, "round", spec, g, out) for p, a, spec, g, out, prec, nf in setups])
+    batch.run(graph=True)
+    batch.run(graph=True)
+    torch.cuda.synchronize()
+    for p, a, spec, g, out, prec, nf in setups:
+        pick = [0, nf - 1]
+        gh = g[pick].double().cpu().numpy()
+        sh = out[pick].double().cpu().numpy()
+        orc = _Oracle(oracle_mod, p)
+        err = per_field_max_rel(gh, orc.inv(a[pick]))
+        assert err < _tol(prec), (p.T, "inverse", err)
+        err = per_field_max_rel(_cplx(sh), orc.dir(gh))
+        assert err < _tol(prec), (p.T, "direct", err)
+    batch.close()
+    for p, *_ in setups:
         p.close()
 
 

@@ -49,14 +49,19 @@ def test_gauss_nodes_match_oracle(st_mod, oracle_mod, nlat):
     assert np.max(np.abs(w.cpu().numpy() - w_o)) <= 2e-16 * max(1.0, nlat / 100)
 
 
-@pytest.mark.parametrize("T,nlat", [(31, 32), (159, 160), (639, 1280)])
+# Both sides run the same three-term recurrence in FP64, so they differ only
+# by rounding, which grows with the degree: 1e-13 normwise up to T = 400, then
+# a bound proportional to T (measured at T639: a few 1e-12; T1279 about twice).
+@pytest.mark.parametrize("T,nlat", [(31, 32), (159, 160), (639, 1280), (1279, 1280), (1279, 2560)])
 def test_legendre_values_match_oracle(st_mod, oracle_mod, T, nlat):
     mu_o, _ = oracle_mod.gauss(nlat)
-    pick = np.unique(np.linspace(0, nlat - 1, 9).astype(int))
+    pick = np.unique(np.concatenate([np.linspace(0, nlat - 1, 9).astype(int), [1, nlat - 2]]))
     P = st_mod.legendre_values(T, torch.from_numpy(mu_o[pick])).cpu().numpy()
+    tol = 1e-13 if T < 400 else 1e-11 * T / 639
     for i, j in enumerate(pick):
         ref = oracle_mod.legendre(T, mu_o[j])
-        assert max_rel(P[i], ref) < (1e-13 if T < 400 else 1e-11), j
+        err = max_rel(P[i], ref)
+        assert err < tol, (j, err)
 
 
 def test_plan_nodes_and_rows(st_mod, oracle_mod):
@@ -155,11 +160,14 @@ def test_round_trip_fp64_regular_identity(st_mod, oracle_mod):
 
 
 def test_fields_independent_and_reusable_plan(st_mod):
-    """A field's result is the same alone and inside a batch (to a few ulps),
-    and repeated calls with different field counts on one plan agree."""
+    """A field's result is bit for bit the same alone and inside a batch, and
+    repeated calls with different field counts on one plan agree: every field
+    takes the same arithmetic in the same order whatever the field count (the
+    GEMMs accumulate each data column alone; an FFT row's fields per CTA only
+    change which slot holds a field)."""
     T = 63
     a = inputs.spectra(T, 40, seed=3)
-    for prec, tol in (("fp64", 1e-14), ("bf16x3", 1e-6)):
+    for prec, tol in (("fp64", 0.0), ("bf16x3", 0.0), ("tf32x3", 0.0)):
         dt = torch.float64 if prec == "fp64" else torch.float32
         p = st_mod.Plan(T, "octahedral", precision=prec, max_fields=40)
         p.inv(_dev(inputs.spectra(T, 40, seed=99), dt))   # leave other data in the workspace
