@@ -500,13 +500,16 @@ def mixed_batch(args, dev):
 
 def serving(args, dev):
     """Serving: T uniform over {63,127,255,511,1279} on regular grids, 1-137
-    fields, inverse or direct with equal odds, Poisson arrivals; BF16x3, tables
-    resident, 4 slots, 32 GB admission budget.  Saturated rate first, then
-    arrivals at 0.5 / 0.7 / 0.9 of it."""
+    fields, inverse or direct with equal odds, Poisson arrivals; BF16x3,
+    tables and 4 slots' workspaces resident, request payloads in a device
+    arena; the device budget is resident + arena.  The saturated rate first
+    (every request present at t = 0: a throughput, no latency), then arrivals
+    at 0.5 / 0.7 / 0.9 of it (10 000 requests at 0.7)."""
     import torch
 
     from paper_1908_06096_gb300 import inputs, serve
-    srv = serve.Server(inputs.SERVE_T, precision="bf16x3", slots=4, max_fields=137, budget_bytes=32 << 30)
+    arena = args.serve_arena_gb << 30
+    srv = serve.Server(inputs.SERVE_T, precision="bf16x3", slots=4, max_fields=137, arena_bytes=arena)
     payloads = {}
     for T, p in srv.base.items():
         payloads[(T, "inv")] = torch.from_numpy(inputs.spectra(T, 137, seed=T)).to(torch.float32).pin_memory()
@@ -514,19 +517,25 @@ def serving(args, dev):
     n = args.serve_requests
     specs = inputs.serve_requests(max(n, 1), seed=1004, rate_hz=1e12)       # all at t = 0
     srv.run(serve.make_requests(specs[:min(200, n)], payloads))              # warm-up
-    sat = srv.run(serve.make_requests(specs, payloads))
+    nsat = min(n, 3000)
+    sat = srv.run(serve.make_requests(specs[:nsat], payloads))
     rate_sat = sat["requests_per_s"]
-    out = {"saturated": sat, "rates": {}}
+    out = {"saturated": {k: sat[k] for k in ("requests", "fields", "wall_s", "requests_per_s",
+                                             "field_transforms_per_s", "peak_inflight_bytes")},
+           "rates": {}}
     for frac in (0.5, 0.7, 0.9):
-        # at most ~20 s of arrivals per rate
-        nr = max(200, min(n, int(frac * rate_sat * 20)))
+        nr = n if frac == 0.7 else min(n, 3000)
         sp = inputs.serve_requests(nr, seed=1004, rate_hz=frac * rate_sat)
-        out["rates"][str(frac)] = srv.run(serve.make_requests(sp, payloads))
-        out["rates"][str(frac)]["rate_hz"] = frac * rate_sat
+        res = srv.run(serve.make_requests(sp, payloads))
+        res["rate_hz"] = frac * rate_sat
+        out["rates"][str(frac)] = res
     out["mix"] = ("T uniform over {63,127,255,511,1279} regular grids, 1-137 fields, inverse or direct 50/50, "
-                  f"Poisson arrivals, up to {n} requests per rate, seed 1004")
-    out["server"] = {"slots": 4, "max_fields_per_call": 137, "budget_bytes": 32 << 30,
-                     "resident_bytes": srv.resident_bytes}
+                  f"Poisson arrivals, {n} requests at 0.7 of saturation, {min(n, 3000)} at 0.5 and 0.9, seed 1004")
+    peak = max([sat["peak_inflight_bytes"]] + [r["peak_inflight_bytes"] for r in out["rates"].values()])
+    out["server"] = {"slots": 4, "max_fields_per_call": 137, "budget_bytes": srv.budget,
+                     "resident_bytes": srv.resident_bytes, "arena_bytes": srv.budget - srv.resident_bytes,
+                     "peak_inflight_bytes": peak,
+                     "peak_inflight_plus_resident_le_budget": peak + srv.resident_bytes <= srv.budget}
     srv.close()
     torch.cuda.empty_cache()
     return out
@@ -579,7 +588,9 @@ def main():
     ap.add_argument("--ref-fields", type=int, default=2)
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-arena-gb", type=int, default=8,
+                    help="device arena for request payloads; the serving budget is resident + arena")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -25,11 +25,13 @@ def _payload(st_mod, plan, T, nf, direction, seed):
     return torch.from_numpy(g).to(torch.float32).pin_memory()
 
 
-@pytest.mark.parametrize("budget_mb", [1024, 3])
-def test_served_results_match_oracle_and_alone(st_mod, oracle_mod, budget_mb):
+# arena for request payloads: roomy, or just above the largest request (T255,
+# 5 fields: about 4 MB) so that admission has to hold requests back
+@pytest.mark.parametrize("arena_mb", [1024, 6])
+def test_served_results_match_oracle_and_alone(st_mod, oracle_mod, arena_mb):
     from paper_1908_06096_gb300 import serve
     Ts = (31, 63, 255)
-    srv = serve.Server(Ts, precision="bf16x3", slots=2, max_fields=12, budget_bytes=budget_mb << 20,
+    srv = serve.Server(Ts, precision="bf16x3", slots=2, max_fields=12, arena_bytes=arena_mb << 20,
                        keep_results=True)
     rng = np.random.default_rng(7)
     reqs = []
@@ -69,27 +71,41 @@ def test_served_results_match_oracle_and_alone(st_mod, oracle_mod, budget_mb):
     srv.close()
 
 
-def test_admission_never_exceeds_budget(st_mod):
+def test_admission_defers_when_the_device_budget_would_be_exceeded(st_mod):
+    """Resident tables and workspaces count against the device budget; a
+    request whose input and output do not fit what is left waits until
+    requests in flight complete, and resident + in-flight never exceeds the
+    budget."""
     from paper_1908_06096_gb300 import serve
-    srv = serve.Server((63,), precision="bf16x3", slots=3, max_fields=16, budget_bytes=0)
+    probe = serve.Server((63,), precision="bf16x3", slots=3, max_fields=16, arena_bytes=1 << 20)
+    resident = probe.resident_bytes
+    one = probe.footprint(serve.Request(0, 0.0, 63, 2, "inv", torch.empty(0)))
+    probe.close()
+    # room for one two-field request in flight (and not for two)
+    budget = resident + one + one // 2
+    srv = serve.Server((63,), precision="bf16x3", slots=3, max_fields=16, budget_bytes=budget)
+    assert srv.resident_bytes == resident
     p = srv.base[63]
-    one_field = srv.footprint(serve.Request(0, 0.0, 63, 1, "inv", torch.empty(0)))
-    srv.budget = 5 * one_field           # room for five fields in flight
     peak = {"v": 0}
     orig = srv._launch
 
-    def spy(slot, batch, ev):
-        inflight = sum(srv.footprint(r) for s in srv.slots for r in s.busy) + \
-            sum(srv.footprint(r) for r in batch)
-        peak["v"] = max(peak["v"], inflight)
-        return orig(slot, batch, ev)
+    def spy(slot, batch, blocks):
+        peak["v"] = max(peak["v"], srv.arena.used * srv.arena.buf.element_size())
+        return orig(slot, batch, blocks)
 
     srv._launch = spy
     reqs = [serve.Request(i, 0.0, 63, 2, "inv", _payload(st_mod, p, 63, 2, "inv", i)) for i in range(12)]
     stats = srv.run(reqs)
     assert stats["requests"] == 12
-    assert 0 < peak["v"] <= srv.budget
-    assert 0 < stats["peak_inflight_bytes"] <= srv.budget
+    assert stats["requests_deferred_for_memory"] > 0
+    assert 0 < peak["v"] <= budget - resident
+    assert stats["resident_bytes"] + stats["peak_inflight_bytes"] <= stats["budget_bytes"] == budget
     # latencies are measured from arrival on the run's own clock
     assert 0 < stats["p50_ms"] <= stats["max_ms"] < 60_000
     srv.close()
+
+
+def test_budget_below_resident_is_refused(st_mod):
+    from paper_1908_06096_gb300 import serve
+    with pytest.raises(serve.AdmissionError):
+        serve.Server((31,), precision="bf16x3", slots=1, max_fields=4, budget_bytes=4096)
