@@ -36,6 +36,9 @@ WORKLOADS = {
     "t159_reg_411": (159, "regular", 160, 320, 411, 1.0, 1001),
     "t639_o640_64": (639, "octahedral", 1280, 0, 64, 1.5, 1002),
     "t31_reg_10": (31, "regular", 32, 64, 10, 1.0, 1000),
+    # the operational resolution of the paper's test cases: TCO1279 on O1280
+    # (2560 Gaussian latitudes, rows 20 + 4i up to 5140 points), 137 levels
+    "t1279_o1280_137": (1279, "octahedral", 2560, 0, 137, 1.5, 1005),
 }
 
 
@@ -231,7 +234,8 @@ def config_of(wl, prec):
     desc = {"t639_o640_548": "T639 octahedral O640 (1280 Gaussian latitudes, rows 20+4i), 137 levels x 4 fields",
             "t159_reg_411": "T159 regular 160 x 320 Gaussian grid, 137 levels x 3 fields",
             "t639_o640_64": "T639 octahedral O640, 64 fields (profiling case)",
-            "t31_reg_10": "T31 regular 32 x 64 Gaussian grid, 10 fields"}[wl]
+            "t31_reg_10": "T31 regular 32 x 64 Gaussian grid, 10 fields",
+            "t1279_o1280_137": "T1279 octahedral O1280 (2560 Gaussian latitudes, rows 20+4i), 137 levels x 1 field"}[wl]
     return {"workload": desc, "T": T, "grid": grid, "nlat": nlat, "nlon": nlon or None, "fields": F,
             "spectra": f"N(0,1) (n+1)^-{p}, seed {seed}", "precision": prec,
             "step": "inverse + direct transform of every field",

@@ -7,7 +7,9 @@ times (all fields in one call), on fields the oracle computes one by one:
   T159 on the regular 160 x 320 grid, 411 fields, FP64 and 3xTF32 — fields
   0 and 410;
   T1279 on the regular 1280 x 2560 grid (the largest truncation the serving
-  mix uses), 16 fields, BF16x3 and FP64 — fields 0 and 15.
+  mix uses), 16 fields, BF16x3 and FP64 — fields 0 and 15;
+  T1279 on O1280 (2560 latitudes, rows 20 + 4i up to 5140 points, FFT lengths
+  up to 8192), 24 fields in BF16x3 and 4 in FP64 — the first and last field.
 
 Inverse: GPU grid of the sampled fields vs the oracle's synthesis of the same
 spectra.  Direct: the sampled fields' grids are replaced by the oracle's
@@ -40,6 +42,8 @@ CASES = [
     (159, "regular", 160, 320, 411, 1.0, 1001, "tf32x3", (0, 410)),
     (1279, "regular", 1280, 2560, 16, 1.0, 1004, "bf16x3", (0, 15)),
     (1279, "regular", 1280, 2560, 16, 1.0, 1004, "fp64", (0, 15)),
+    (1279, "octahedral", 2560, 0, 24, 1.5, 1005, "bf16x3", (0, 23)),
+    (1279, "octahedral", 2560, 0, 4, 1.5, 1005, "fp64", (0, 3)),
 ]
 
 
