@@ -66,6 +66,13 @@ def _load():
                                                      ctypes.c_int, _D, ctypes.c_int]
             lib.or_dir_trans.argtypes = [ctypes.c_int, ctypes.c_int, _I, _D, _D, _D,
                                          ctypes.c_int, _D, ctypes.c_int]
+            lib.or_legendre_deriv.argtypes = [ctypes.c_int, ctypes.c_double, _D]
+            lib.or_inv_trans_deriv.argtypes = [ctypes.c_int, ctypes.c_int, _I, _D, _D, ctypes.c_int,
+                                               _D, _D, ctypes.c_int]
+            lib.or_inv_trans_uv.argtypes = [ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, ctypes.c_int,
+                                            _D, _D, ctypes.c_int]
+            lib.or_dir_trans_vordiv.argtypes = [ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D,
+                                                ctypes.c_int, _D, _D, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -86,7 +93,8 @@ class use_library:
         lib = ctypes.CDLL(self.path)
         for fn in ("or_nspec", "or_grid_rows", "or_gauss", "or_legendre", "or_max_threads",
                    "or_inv_fourier", "or_inv_grid_from_fourier", "or_inv_trans",
-                   "or_dir_fourier", "or_dir_spec_from_fourier", "or_dir_trans"):
+                   "or_dir_fourier", "or_dir_spec_from_fourier", "or_dir_trans",
+                   "or_legendre_deriv", "or_inv_trans_deriv", "or_inv_trans_uv", "or_dir_trans_vordiv"):
             src = getattr(self.saved, fn)
             dst = getattr(lib, fn)
             dst.argtypes = src.argtypes
@@ -243,3 +251,57 @@ def dir_trans(T, rows, mu, w, grid, nthreads=0):
     _check(_load().or_dir_trans(T, nlat, _ip(rows), _dp(mu), _dp(w), _dp(g), nf, _dp(out), nthreads),
            "dir_trans")
     return out[..., 0] + 1j * out[..., 1]
+
+
+# ---------------------------------------------------------------- derivatives
+# Readings: unit sphere, phi the latitude (mu = sin phi); H_n^m = (1 - mu^2)
+# dPbar_n^m/dmu; wind images U = u cos(phi), V = v cos(phi).
+
+def legendre_deriv(T: int, mu: float) -> np.ndarray:
+    """All H_n^m(mu) = (1 - mu^2) dPbar_n^m/dmu, n <= T, triangular order."""
+    H = np.zeros(nspec(T))
+    _check(_load().or_legendre_deriv(T, float(mu), _dp(H)), "legendre_deriv")
+    return H
+
+
+def inv_trans_deriv(T, rows, mu, spec, nthreads=0):
+    """(dF/dlambda, (1 - mu^2) dF/dmu) on the grid, each [nf, sum(rows)]."""
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    s = _spec_arr(spec, T)
+    nf, nlat = s.shape[0], len(rows)
+    a = np.zeros((nf, int(rows.sum())))
+    b = np.zeros((nf, int(rows.sum())))
+    _check(_load().or_inv_trans_deriv(T, nlat, _ip(rows), _dp(mu), _dp(s), nf, _dp(a), _dp(b), nthreads),
+           "inv_trans_deriv")
+    return a, b
+
+
+def inv_trans_uv(T, rows, mu, vor, div, nthreads=0):
+    """Wind images (U, V) = (u cos phi, v cos phi) from vorticity and divergence spectra."""
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    z = _spec_arr(vor, T)
+    d = _spec_arr(div, T)
+    nf, nlat = z.shape[0], len(rows)
+    U = np.zeros((nf, int(rows.sum())))
+    V = np.zeros((nf, int(rows.sum())))
+    _check(_load().or_inv_trans_uv(T, nlat, _ip(rows), _dp(mu), _dp(z), _dp(d), nf, _dp(U), _dp(V), nthreads),
+           "inv_trans_uv")
+    return U, V
+
+
+def dir_trans_vordiv(T, rows, mu, w, U, V, nthreads=0):
+    """Vorticity and divergence spectra ([nf, nspec] complex each) from wind images U, V."""
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    npts = int(rows.sum())
+    U = np.ascontiguousarray(U, dtype=np.float64).reshape(-1, npts)
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1, npts)
+    nf, nlat = U.shape[0], len(rows)
+    z = np.zeros((nf, nspec(T), 2))
+    d = np.zeros((nf, nspec(T), 2))
+    _check(_load().or_dir_trans_vordiv(T, nlat, _ip(rows), _dp(mu), _dp(w), _dp(U), _dp(V), nf, _dp(z), _dp(d),
+                                       nthreads), "dir_trans_vordiv")
+    return z[..., 0] + 1j * z[..., 1], d[..., 0] + 1j * d[..., 1]

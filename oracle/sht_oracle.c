@@ -400,3 +400,222 @@ int or_dir_trans(int T, int nlat, const int *rows, const double *mu, const doubl
     free(four);
     return e;
 }
+
+/* ------------------------------------------------------------------ derivatives
+ *
+ * Readings for the derivative and wind transforms of the SH dwarf's time step
+ * (the paper names them, it prints no formula): the unit sphere, phi the
+ * latitude (mu = sin(phi)), and
+ *   H_n^m(mu) = (1 - mu^2) dPbar_n^m/dmu,
+ * which stays finite at the poles.  With eps_n^m = sqrt((n^2 - m^2)/(4 n^2 - 1))
+ * the normalised functions satisfy
+ *   H_n^m = (n + 1) eps_n^m Pbar_{n-1}^m - n eps_{n+1}^m Pbar_{n+1}^m
+ * (Pbar_{m-1}^m = 0), the textbook relation of P_n^m' to P_{n-1}^m and
+ * P_{n+1}^m divided by the normalisation constants. */
+static double eps_nm(int n, int m)
+{
+    if (n <= m) return 0.0;
+    return sqrt(((double)n * n - (double)m * m) / (4.0 * n * n - 1.0));
+}
+
+/* H_n^m(mu) for all 0 <= m <= n <= T in the triangular order of T. */
+int or_legendre_deriv(int T, double mu, double *H)
+{
+    if (T < 0) return 1;
+    long n1 = or_nspec(T + 1);
+    double *P = (double *)malloc(sizeof(double) * n1);
+    if (!P) return 2;
+    or_legendre(T + 1, mu, P);
+    for (int m = 0; m <= T; ++m)
+        for (int n = m; n <= T; ++n) {
+            double pm1 = n - 1 >= m ? P[spec_index(T + 1, m, n - 1)] : 0.0;
+            double pp1 = P[spec_index(T + 1, m, n + 1)];
+            H[spec_index(T, m, n)] = (n + 1.0) * eps_nm(n, m) * pm1 - (double)n * eps_nm(n + 1, m) * pp1;
+        }
+    free(P);
+    return 0;
+}
+
+/* Fourier coefficients of the two derivative fields of every row:
+ *   dF/dlambda:            G_m = sum_n i m a_n^m Pbar_n^m(mu_j)
+ *   (1 - mu^2) dF/dmu:     K_m = sum_n a_n^m H_n^m(mu_j)
+ * for m <= M_j.  Layout as or_inv_fourier, twice. */
+static int deriv_fourier(int T, int nlat, const int *rows, const double *mu, const double *spec, int nf,
+                         double *G, double *K)
+{
+    long nspec = or_nspec(T);
+    int err = 0;
+#pragma omp parallel
+    {
+        double *P = (double *)malloc(sizeof(double) * nspec);
+        double *H = (double *)malloc(sizeof(double) * nspec);
+        if (!P || !H) {
+#pragma omp atomic write
+            err = 2;
+        }
+#pragma omp for schedule(dynamic)
+        for (int j = 0; j < nlat; ++j) {
+            if (!P || !H) continue;
+            or_legendre(T, mu[j], P);
+            or_legendre_deriv(T, mu[j], H);
+            int mj = row_trunc(T, rows[j]);
+            for (int f = 0; f < nf; ++f) {
+                const double *a = spec + (long)f * nspec * 2;
+                double *g = G + ((long)f * nlat + j) * (T + 1) * 2;
+                double *k = K + ((long)f * nlat + j) * (T + 1) * 2;
+                for (int m = 0; m <= T; ++m) {
+                    double pr = 0.0, pi = 0.0, hr = 0.0, hi = 0.0;
+                    if (m <= mj) {
+                        for (int n = m; n <= T; ++n) {
+                            long q = spec_index(T, m, n);
+                            pr += a[2 * q] * P[q];
+                            pi += a[2 * q + 1] * P[q];
+                            hr += a[2 * q] * H[q];
+                            hi += a[2 * q + 1] * H[q];
+                        }
+                    }
+                    /* i m (pr + i pi) */
+                    g[2 * m] = -(double)m * pi;
+                    g[2 * m + 1] = (double)m * pr;
+                    k[2 * m] = hr;
+                    k[2 * m + 1] = hi;
+                }
+            }
+        }
+        free(P);
+        free(H);
+    }
+    return err;
+}
+
+/* dF/dlambda and (1 - mu^2) dF/dmu (= cos(phi) dF/dphi) of each field on the
+ * grid, from its spectra; out_dlam, out_dmu: [nf][npts]. */
+int or_inv_trans_deriv(int T, int nlat, const int *rows, const double *mu, const double *spec, int nf,
+                       double *out_dlam, double *out_dmu, int nthreads)
+{
+    size_t n4 = (size_t)nf * nlat * (T + 1) * 2;
+    double *G = (double *)malloc(sizeof(double) * n4);
+    double *K = (double *)malloc(sizeof(double) * n4);
+    int e = (!G || !K) ? 2 : 0;
+    set_threads(nthreads);
+    if (!e) e = deriv_fourier(T, nlat, rows, mu, spec, nf, G, K);
+    if (!e) e = or_inv_grid_from_fourier(T, nlat, rows, G, nf, out_dlam, nthreads);
+    if (!e) e = or_inv_grid_from_fourier(T, nlat, rows, K, nf, out_dmu, nthreads);
+    free(G);
+    free(K);
+    return e;
+}
+
+/* Wind images U = u cos(phi), V = v cos(phi) on the grid from vorticity and
+ * divergence spectra (vor, div: [nf][nspec][re, im]):
+ *   psi_n^m = -zeta_n^m / (n (n + 1)),  chi_n^m = -D_n^m / (n (n + 1))  (0 at n = 0)
+ *   U = dchi/dlambda - (1 - mu^2) dpsi/dmu,   V = dpsi/dlambda + (1 - mu^2) dchi/dmu. */
+int or_inv_trans_uv(int T, int nlat, const int *rows, const double *mu, const double *vor, const double *div,
+                    int nf, double *U, double *V, int nthreads)
+{
+    long nspec = or_nspec(T);
+    long npts = 0;
+    for (int j = 0; j < nlat; ++j) npts += rows[j];
+    size_t ns = (size_t)nf * nspec * 2;
+    double *psi = (double *)malloc(sizeof(double) * ns);
+    double *chi = (double *)malloc(sizeof(double) * ns);
+    double *a = (double *)malloc(sizeof(double) * (size_t)nf * npts);
+    double *b = (double *)malloc(sizeof(double) * (size_t)nf * npts);
+    int e = (!psi || !chi || !a || !b) ? 2 : 0;
+    if (!e) {
+        for (int f = 0; f < nf; ++f)
+            for (int m = 0; m <= T; ++m)
+                for (int n = m; n <= T; ++n) {
+                    long q = (long)f * nspec + spec_index(T, m, n);
+                    double s = n == 0 ? 0.0 : -1.0 / ((double)n * (n + 1.0));
+                    psi[2 * q] = s * vor[2 * q];
+                    psi[2 * q + 1] = s * vor[2 * q + 1];
+                    chi[2 * q] = s * div[2 * q];
+                    chi[2 * q + 1] = s * div[2 * q + 1];
+                }
+        /* U: dchi/dlambda into U, (1 - mu^2) dpsi/dmu into b */
+        e = or_inv_trans_deriv(T, nlat, rows, mu, chi, nf, U, a, nthreads);
+        if (!e) e = or_inv_trans_deriv(T, nlat, rows, mu, psi, nf, V, b, nthreads);
+        /* now U = dchi/dlambda, a = (1-mu^2) dchi/dmu, V = dpsi/dlambda, b = (1-mu^2) dpsi/dmu */
+        if (!e)
+            for (size_t i = 0; i < (size_t)nf * npts; ++i) {
+                U[i] -= b[i];
+                V[i] += a[i];
+            }
+    }
+    free(psi);
+    free(chi);
+    free(a);
+    free(b);
+    return e;
+}
+
+/* Vorticity and divergence spectra from wind images U = u cos(phi),
+ * V = v cos(phi) on the grid ([nf][npts]):
+ *   zeta = (1 / (1 - mu^2)) (dV/dlambda - (1 - mu^2) dU/dmu),
+ *   D    = (1 / (1 - mu^2)) (dU/dlambda + (1 - mu^2) dV/dmu),
+ * projected on each basis function with the mu-derivative moved onto Pbar by
+ * parts (U and V vanish at the poles):
+ *   zeta_n^m = sum_j w_j / (1 - mu_j^2) (i m V_m Pbar_n^m + U_m H_n^m),
+ *   D_n^m    = sum_j w_j / (1 - mu_j^2) (i m U_m Pbar_n^m - V_m H_n^m),
+ * U_m, V_m the rows' Fourier coefficients (1/N_j sum_k e^{-i m lambda_k}). */
+int or_dir_trans_vordiv(int T, int nlat, const int *rows, const double *mu, const double *w, const double *U,
+                        const double *V, int nf, double *vor, double *div, int nthreads)
+{
+    long nspec = or_nspec(T);
+    size_t n4 = (size_t)nf * nlat * (T + 1) * 2;
+    double *FU = (double *)malloc(sizeof(double) * n4);
+    double *FV = (double *)malloc(sizeof(double) * n4);
+    int e = (!FU || !FV) ? 2 : 0;
+    if (!e) e = or_dir_fourier(T, nlat, rows, U, nf, FU, nthreads);
+    if (!e) e = or_dir_fourier(T, nlat, rows, V, nf, FV, nthreads);
+    set_threads(nthreads);
+    if (!e) {
+#pragma omp parallel
+        {
+            double *P = (double *)malloc(sizeof(double) * nspec);
+            double *H = (double *)malloc(sizeof(double) * nspec);
+            if (!P || !H) {
+#pragma omp atomic write
+                e = 2;
+            }
+#pragma omp for schedule(dynamic)
+            for (int f = 0; f < nf; ++f) {
+                if (!P || !H) continue;
+                double *z = vor + (long)f * nspec * 2;
+                double *d = div + (long)f * nspec * 2;
+                memset(z, 0, sizeof(double) * nspec * 2);
+                memset(d, 0, sizeof(double) * nspec * 2);
+                for (int j = 0; j < nlat; ++j) {
+                    or_legendre(T, mu[j], P);
+                    or_legendre_deriv(T, mu[j], H);
+                    double c = w[j] / ((1.0 - mu[j]) * (1.0 + mu[j]));
+                    const double *u = FU + ((long)f * nlat + j) * (T + 1) * 2;
+                    const double *v = FV + ((long)f * nlat + j) * (T + 1) * 2;
+                    for (int m = 0; m <= T; ++m) {
+                        /* i m V_m and i m U_m */
+                        double imvr = -(double)m * v[2 * m + 1], imvi = (double)m * v[2 * m];
+                        double imur = -(double)m * u[2 * m + 1], imui = (double)m * u[2 * m];
+                        for (int n = m; n <= T; ++n) {
+                            long q = spec_index(T, m, n);
+                            z[2 * q] += c * (imvr * P[q] + u[2 * m] * H[q]);
+                            z[2 * q + 1] += c * (imvi * P[q] + u[2 * m + 1] * H[q]);
+                            d[2 * q] += c * (imur * P[q] - v[2 * m] * H[q]);
+                            d[2 * q + 1] += c * (imui * P[q] - v[2 * m + 1] * H[q]);
+                        }
+                    }
+                }
+                /* Im of m = 0 coefficients is zero for real fields */
+                for (int n = 0; n <= T; ++n) {
+                    z[2 * spec_index(T, 0, n) + 1] = 0.0;
+                    d[2 * spec_index(T, 0, n) + 1] = 0.0;
+                }
+            }
+            free(P);
+            free(H);
+        }
+    }
+    free(FU);
+    free(FV);
+    return e;
+}

@@ -29,6 +29,18 @@ MUTATIONS = {
     # quadrature weight dropped in the analysis
     "no_weight": ("double fr = w[j] * F[2 * m], fi = w[j] * F[2 * m + 1];",
                   "double fr = F[2 * m], fi = F[2 * m + 1];"),
+    # derivative relation: wrong sign of the Pbar_{n+1} term
+    "deriv_sign": ("H[spec_index(T, m, n)] = (n + 1.0) * eps_nm(n, m) * pm1 - (double)n * eps_nm(n + 1, m) * pp1;",
+                   "H[spec_index(T, m, n)] = (n + 1.0) * eps_nm(n, m) * pm1 + (double)n * eps_nm(n + 1, m) * pp1;"),
+    # derivative relation: eps index off by one
+    "deriv_eps": ("H[spec_index(T, m, n)] = (n + 1.0) * eps_nm(n, m) * pm1 - (double)n * eps_nm(n + 1, m) * pp1;",
+                  "H[spec_index(T, m, n)] = (n + 1.0) * eps_nm(n + 1, m) * pm1 - (double)n * eps_nm(n, m) * pp1;"),
+    # d/dlambda as -i m instead of i m
+    "dlam_sign": ("g[2 * m] = -(double)m * pi;", "g[2 * m] = (double)m * pi;"),
+    # wind: V built with the wrong sign of the chi term
+    "wind_sign": ("V[i] += a[i];", "V[i] -= a[i];"),
+    # vorticity analysis without the 1 / (1 - mu^2) factor
+    "vordiv_cos": ("double c = w[j] / ((1.0 - mu[j]) * (1.0 + mu[j]));", "double c = w[j];"),
     # spectral index with m and n swapped in the triangle offset
     "spec_index": ("return (long)m * (T + 1) - (long)m * (m - 1) / 2 + (n - m);",
                    "return (long)m * (T + 1) - (long)m * (m + 1) / 2 + (n - m);"),
@@ -44,6 +56,11 @@ PIN_CALLS = [
     lambda o: pins.test_single_mode(o, 3, 7, 1j),
     lambda o: pins.test_round_trip_regular(o, 15),
     lambda o: pins.test_parseval_regular(o),
+    lambda o: pins.test_derivative_closed_forms(o, 0.41),
+    lambda o: pins.test_derivative_values_match_finite_differences(o, 0.05),
+    lambda o: pins.test_derivative_synthesis_matches_finite_differences(o),
+    lambda o: pins.test_solid_body_rotation(o),
+    lambda o: pins.test_wind_round_trip(o, 15, 16),
 ]
 
 

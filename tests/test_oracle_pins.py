@@ -302,3 +302,85 @@ def test_regular_grid_rule(oracle_mod):
     assert rows.shape == (160,) and np.all(rows == 320)
     with pytest.raises(RuntimeError):
         oracle_mod.grid_rows("regular", 31, 64)      # odd number of latitudes
+
+
+# ---------------------------------------------------------------- derivatives
+# Readings (the paper names the derivative and wind transforms of the time
+# step but prints no formula): unit sphere, phi the latitude (mu = sin phi),
+# H_n^m = (1 - mu^2) dPbar_n^m/dmu, wind images U = u cos(phi), V = v cos(phi),
+# psi = -zeta / (n (n+1)), chi = -D / (n (n+1)).
+
+@pytest.mark.parametrize("x", [-0.93, -0.2, 0.0, 0.41, 0.97])
+def test_derivative_closed_forms(oracle_mod, x):
+    q = oracle_mod.spec_index
+    H = oracle_mod.legendre_deriv(3, x)
+    s = math.sqrt(1 - x * x)
+    assert abs(H[q(3, 0, 0)]) < 1e-15                                      # constant
+    assert abs(H[q(3, 0, 1)] - math.sqrt(1.5) * (1 - x * x)) < 1e-14        # sqrt(3/2) mu
+    assert abs(H[q(3, 1, 1)] + math.sqrt(3) / 2 * x * s) < 1e-14           # (sqrt 3 / 2) sin theta
+    assert abs(H[q(3, 0, 2)] - math.sqrt(2.5) * 3 * x * (1 - x * x)) < 1e-14  # sqrt(5/2) (3 mu^2 - 1)/2
+
+
+@pytest.mark.parametrize("x", [-0.7, 0.05, 0.6])
+def test_derivative_values_match_finite_differences(oracle_mod, x):
+    """H from the recurrence relation against a central difference of the
+    oracle's own Pbar (fourth order), every (m, n) up to T = 12."""
+    T, h = 12, 3e-4               # truncation error ~ h^4, about 1e-10 here
+    P = [oracle_mod.legendre(T, x + k * h) for k in (-2, -1, 1, 2)]
+    dP = (P[0] - 8 * P[1] + 8 * P[2] - P[3]) / (12 * h)
+    H = oracle_mod.legendre_deriv(T, x)
+    assert np.max(np.abs(H - (1 - x * x) * dP)) < 1e-9
+
+
+def test_derivative_synthesis_matches_finite_differences(oracle_mod):
+    """d/dlambda against a centred difference of the synthesis of the spectra
+    rotated by +-delta (a_n^m e^{+-i m delta}); (1 - mu^2) d/dmu against a
+    centred difference of the synthesis at mu +- delta.  Neither reference
+    touches the derivative code."""
+    T, nlat = 15, 16
+    rows = oracle_mod.grid_rows("regular", nlat, 32)
+    mu, _ = oracle_mod.gauss(nlat)
+    a = inputs.spectra(T, 2, seed=41)
+    ac = a[..., 0] + 1j * a[..., 1]
+    m_of = inputs.order_of_index(T)
+    dl, dm = oracle_mod.inv_trans_deriv(T, rows, mu, a)
+    d = 1e-4                      # fourth-order differences: truncation error ~ 1e-10 here
+
+    def diff4(f):
+        return (f(-2) - 8 * f(-1) + 8 * f(1) - f(2)) / (12 * d)
+
+    ref = diff4(lambda k: oracle_mod.inv_trans(T, rows, mu, ac * np.exp(1j * m_of * k * d)))
+    assert np.max(np.abs(dl - ref)) / np.max(np.abs(ref)) < 1e-8
+    w1 = np.repeat(1 - mu * mu, rows)
+    ref = w1 * diff4(lambda k: oracle_mod.inv_trans(T, rows, mu + k * d, a))
+    assert np.max(np.abs(dm - ref)) / np.max(np.abs(ref)) < 1e-8
+
+
+def test_solid_body_rotation(oracle_mod):
+    """Vorticity 2 Omega mu (zeta_1^0 = 2 Omega sqrt(2/3)) is the rotation
+    u = Omega cos(phi), v = 0: U = Omega (1 - mu^2), V = 0."""
+    T, nlat, om = 10, 12, 0.7
+    rows = oracle_mod.grid_rows("regular", nlat, 24)
+    mu, _ = oracle_mod.gauss(nlat)
+    z = np.zeros((1, oracle_mod.nspec(T)), complex)
+    z[0, oracle_mod.spec_index(T, 0, 1)] = 2 * om * math.sqrt(2.0 / 3.0)
+    U, V = oracle_mod.inv_trans_uv(T, rows, mu, z, np.zeros_like(z))
+    assert np.max(np.abs(U[0] - om * np.repeat(1 - mu * mu, rows))) < 1e-14
+    assert np.max(np.abs(V)) < 1e-14
+
+
+@pytest.mark.parametrize("T,nlat", [(15, 16), (31, 48)])
+def test_wind_round_trip(oracle_mod, T, nlat):
+    """Vorticity and divergence -> wind images -> vorticity and divergence is
+    the identity on regular Gaussian grids (n = 0 terms zero)."""
+    rows = oracle_mod.grid_rows("regular", nlat, 2 * nlat)
+    mu, w = oracle_mod.gauss(nlat)
+    z = inputs.spectra(T, 3, seed=51)
+    dv = inputs.spectra(T, 3, seed=52)
+    zc, dc = z[..., 0] + 1j * z[..., 1], dv[..., 0] + 1j * dv[..., 1]
+    zc[:, 0] = 0
+    dc[:, 0] = 0
+    U, V = oracle_mod.inv_trans_uv(T, rows, mu, zc, dc)
+    z2, d2 = oracle_mod.dir_trans_vordiv(T, rows, mu, w, U, V)
+    assert np.max(np.abs(z2 - zc)) / np.max(np.abs(zc)) < 1e-13
+    assert np.max(np.abs(d2 - dc)) / np.max(np.abs(dc)) < 1e-13
