@@ -193,6 +193,42 @@ st_status st_dir_trans(st_plan_t plan, const void *grid_dev, void *spec_dev, int
 st_status st_inv_trans_static(st_plan_t plan, const void *spec_dev, void *grid_dev, int nfields,
                               void *stream);
 
+/*
+ * Derivative and wind transforms, the other transforms of the SH dwarf's time
+ * step (ESCAPE D3.3 sections 4.2.2-4.2.3 name them; the formulas are the
+ * standard ones, stated here).  Unit sphere, phi the latitude, mu = sin(phi),
+ * H_n^m = (1 - mu^2) dPbar_n^m/dmu; wind images U = u cos(phi), V = v cos(phi);
+ * stream function psi = -zeta / (n (n+1)) and velocity potential
+ * chi = -D / (n (n+1)) from vorticity zeta and divergence D (0 for n = 0).
+ *
+ * st_plan_enable_derivatives builds, once per plan and in FP64 on the device,
+ * three more Legendre table sets in the plan's precision (H for synthesis,
+ * w_j Pbar / (1 - mu_j^2) and w_j H / (1 - mu_j^2) for analysis) and a second
+ * Fourier buffer and spectral output.  Synchronous; ST_ERR_OOM if they do not
+ * fit.  The calls below need it, and need 2 nfields <= max_fields (they run
+ * the FFT and Legendre stages on 2 nfields column pairs); ST_ERR_ARG otherwise.
+ * Same layouts, element type and asynchrony as st_inv_trans / st_dir_trans.
+ */
+st_status st_plan_enable_derivatives(st_plan_t plan, void *stream);
+
+/* out_dev [2 nfields][grid]: fields 0 .. nfields-1 are dF/dlambda, fields
+ * nfields .. 2 nfields-1 are (1 - mu^2) dF/dmu = cos(phi) dF/dphi of the
+ * nfields spectra in spec_dev. */
+st_status st_inv_trans_deriv(st_plan_t plan, const void *spec_dev, void *out_dev, int nfields, void *stream);
+
+/* vordiv_dev [2 nfields][spectra]: vorticity fields, then divergence fields;
+ * uv_dev [2 nfields][grid] receives U fields, then V fields:
+ *   U = dchi/dlambda - (1 - mu^2) dpsi/dmu,  V = dpsi/dlambda + (1 - mu^2) dchi/dmu. */
+st_status st_inv_trans_uv(st_plan_t plan, const void *vordiv_dev, void *uv_dev, int nfields, void *stream);
+
+/* The reverse: uv_dev [2 nfields][grid] (U fields, then V fields) ->
+ * vordiv_dev [2 nfields][spectra] (vorticity, then divergence), by Gaussian
+ * quadrature with the mu-derivative moved onto Pbar by parts:
+ *   zeta_n^m = sum_j w_j / (1 - mu_j^2) (i m V_m Pbar_n^m + U_m H_n^m),
+ *   D_n^m    = sum_j w_j / (1 - mu_j^2) (i m U_m Pbar_n^m - V_m H_n^m),
+ * U_m, V_m the rows' Fourier coefficients (1/N_j sum_k e^{-i m lambda_k}). */
+st_status st_dir_trans_vordiv(st_plan_t plan, const void *uv_dev, void *vordiv_dev, int nfields, void *stream);
+
 /* Size in bytes of the array st_inv_trans_static uses. */
 size_t st_static_scratch_bytes(void);
 

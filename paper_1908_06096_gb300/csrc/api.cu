@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 
 namespace st {
 
@@ -148,6 +149,8 @@ static st_status dmalloc(st_plan *p, T **ptr, size_t bytes)
     return ST_OK;
 }
 
+st_status plan_alloc(st_plan *p, void **ptr, size_t bytes) { return dmalloc(p, ptr, bytes); }
+
 // Owner of a plan's read-only device arrays (shared between plans).
 struct TableCore {
     std::vector<void *> ptrs;
@@ -161,9 +164,14 @@ struct TableCore {
 static void plan_free(st_plan *p)
 {
     if (!p) return;
-    void *ws[] = {p->fb, p->fbop, p->sop, p->sout, p->err};
+    void *ws[] = {p->fb, p->fbop, p->sop, p->sout, p->err, p->fb2, p->sout2};
     for (void *q : ws)
         if (q) cudaFree(q);
+    // derivative table sets are the plan's own
+    for (int set = SET_SYN_H; set < NSETS; ++set) {
+        if (p->tab[set]) cudaFree(p->tab[set]);
+        if (p->groups[set]) cudaFree(p->groups[set]);
+    }
     if (!p->core) {
         // creation failed before the read-only arrays were handed to a core
         void *ro[] = {p->mu, p->w, p->rowpairs, p->tw, p->chirp, p->kern, p->tab[0], p->tab[1], p->groups[0],
@@ -249,6 +257,20 @@ static void build_groups(st_plan *p, int dir)
     }
     const size_t el = tc ? 1 : (p->prec == P_FP64 ? 8 : 4);
     p->tab_bytes[dir] = (size_t)off * el;
+}
+
+// Groups of a derivative table set: the geometry (and so the table layout)
+// of its direction's base set, with the Fourier-buffer halves exchanged on
+// the H sets (H_n^m has the opposite parity in mu to Pbar_n^m).
+void build_groups_deriv(st_plan *p, int set)
+{
+    const int base = set_dir(set);
+    p->groups_h[set] = p->groups_h[base];
+    if (set == SET_SYN_H)
+        for (auto &g : p->groups_h[set]) g.out_row0 = fb_row(p, 1 - g.p, g.m, 0);
+    if (set == SET_ANA_H1)
+        for (auto &g : p->groups_h[set]) g.data_row0 = fb_row(p, 1 - g.p, g.m, 0);
+    p->tab_bytes[set] = p->tab_bytes[base];
 }
 
 // Work list (group, column tile), heaviest first.
@@ -339,6 +361,18 @@ st_status rebuild_legendre(st_plan *p, cudaStream_t s)
         core->ptrs.push_back(p->tiles[dir]);
     }
     if ((r = launch_tables(p, s))) return r;
+    if (p->deriv) {
+        for (int set = SET_SYN_H; set < NSETS; ++set) {
+            build_groups_deriv(p, set);
+            ST_CUDA(cudaMemcpy(p->groups[set], p->groups_h[set].data(), sizeof(LegGroup) * p->groups_h[set].size(),
+                               cudaMemcpyHostToDevice));
+            if (p->tab[set]) cudaFree(p->tab[set]);
+            p->tab[set] = nullptr;
+            if ((r = dmalloc(p, &p->tab[set], p->tab_bytes[set]))) return r;
+            ST_CUDA(cudaMemsetAsync(p->tab[set], 0, std::max<size_t>(p->tab_bytes[set], 16), s));
+        }
+        if ((r = launch_tables_deriv(p, s))) return r;
+    }
     ST_CUDA(cudaStreamSynchronize(s));
     return ST_OK;
 }
@@ -602,6 +636,7 @@ const char *kernel_name(const st_plan *p, int kind)
     case K_UNPACK: return "unpack_spectra";
     case K_EXPORT: return "fourier_export";
     case K_TABLES: return "plan_tables";
+    case K_COMBINE: return "derivative_combine";
     }
     return "?";
 }
@@ -639,6 +674,11 @@ static st_status counted(st_plan *p, int kind, cudaStream_t s, F f)
         if (b) p->event_pool.push_back(b);
     }
     return r;
+}
+
+st_status count_launch(st_plan *p, int kind, cudaStream_t s, const std::function<st_status()> &f)
+{
+    return counted(p, kind, s, f);
 }
 
 static st_status leg(st_plan *p, int dir, int nfields, cudaStream_t s)

@@ -177,12 +177,13 @@ st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t
     return launch_fft_jobs(1, p->prec, jobs.data(), (int)jobs.size(), smem, s, p->fft_var[1]);
 }
 
-st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb_in)
+st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb_in, int a_top)
 {
     std::vector<FftJob> jobs;
     size_t smem = 0;
     st_status r = fft_jobs(p, 0, nfields, fb_in ? fb_in : p->fb, grid, jobs, &smem);
     if (r) return r;
+    for (auto &J : jobs) J.a_top = a_top;
     return launch_fft_jobs(0, p->prec, jobs.data(), (int)jobs.size(), smem, s, p->fft_var[0]);
 }
 

@@ -632,12 +632,12 @@ __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0
                 // The odd-parity half of m = T is empty (no n = T + 1): A = 0 there.
                 if (two) {
                     sv[u] = *(const float4 *)(fb + rS);
-                    if (m < T) av[u] = *(const float4 *)(fb + rA);
+                    if (m < T || J.a_top) av[u] = *(const float4 *)(fb + rA);
                 } else {
                     const float2 s2 = *(const float2 *)(fb + rS);
                     sv[u].x = s2.x;
                     sv[u].y = s2.y;
-                    if (m < T) {
+                    if (m < T || J.a_top) {
                         const float2 a2 = *(const float2 *)(fb + rA);
                         av[u].x = a2.x;
                         av[u].y = a2.y;

@@ -777,7 +777,7 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
                     const long long rS = ((long long)m * Jp + j) * Cp + 2 * fld;
                     const long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * fld;
                     sv[u] = *(const float4 *)((const float *)fb + rS);
-                    if (m < T) av[u] = *(const float4 *)((const float *)fb + rA);
+                    if (m < T || J.a_top) av[u] = *(const float4 *)((const float *)fb + rA);
                     if (rp.mode == 1) cw[u] = __ldg(&chirp[m]);  // w_{-m} = w_m
                 }
             }
@@ -835,7 +835,7 @@ __device__ inline void fft_inv_body(const FftJob &J, const RowPair &rp, int j, i
                 sv[u] = *(const C2 *)(fb + rS);
                 // the odd-parity half of m = T is empty (no n = T + 1), so its
                 // rows are never written by the Legendre stage: A = 0 there
-                if (m < T) av[u] = *(const C2 *)(fb + rA);
+                if (m < T || J.a_top) av[u] = *(const C2 *)(fb + rA);
                 if (rp.mode == 1) {
                     ca[u] = __ldg(&chirp[m]);  // w_{-m} = w_m
                     cb[u] = ca[u];

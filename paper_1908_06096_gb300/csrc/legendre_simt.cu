@@ -80,17 +80,19 @@ __global__ void __launch_bounds__(256) k_leg_simt(const __grid_constant__ SimtBa
     }
 }
 
-st_status simt_job(st_plan *p, int dir, int nfields, const void *data, void *out, SimtJob *job, long long *blocks)
+st_status simt_job(st_plan *p, int set, int nfields, const void *data, void *out, SimtJob *job, long long *blocks,
+                   int cp)
 {
-    job->groups = p->groups[dir];
-    job->tiles = p->tiles[dir];
-    job->tab = p->tab[dir];
+    const int td = set_dir(set);
+    job->groups = p->groups[set];
+    job->tiles = p->tiles[td];
+    job->tab = p->tab[set];
     job->data = data;
     job->out = out;
     job->C = 2 * nfields;
-    job->Cp = cols_padded(nfields);
+    job->Cp = cp ? cp : cols_padded(nfields);
     job->ncm = (job->C + SIMT_TILE - 1) / SIMT_TILE;
-    *blocks = (long long)p->ntiles[dir] * job->ncm;
+    *blocks = (long long)p->ntiles[td] * job->ncm;
     return ST_OK;
 }
 
@@ -122,6 +124,20 @@ st_status launch_simt_jobs(int prec, const SimtJob *jobs, const long long *block
                               : run_simt_batch<1>(k_leg_simt<float, 1>, jobs, blocks, n, s);
     return prec == P_FP64 ? run_simt_batch<MAX_JOBS>(k_leg_simt<double, MAX_JOBS>, jobs, blocks, n, s)
                           : run_simt_batch<MAX_JOBS>(k_leg_simt<float, MAX_JOBS>, jobs, blocks, n, s);
+}
+
+st_status launch_leg_set(st_plan *p, int set, int nfields, cudaStream_t s, void *data, void *out, int cp)
+{
+    if (prec_is_tc(p->prec)) {
+        TcJob J;
+        st_status r = tc_job(p, set, nfields, data, out, &J, cp);
+        if (r) return r;
+        return launch_tc_jobs(p->prec, &J, 1, p->sm_count, s);
+    }
+    SimtJob J;
+    long long blocks = 0;
+    simt_job(p, set, nfields, data, out, &J, &blocks, cp);
+    return launch_simt_jobs(p->prec, &J, &blocks, 1, s);
 }
 
 st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s, void *data_in, void *out_in)
@@ -193,6 +209,13 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ PackBatch<
                 const Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
                 re = a[0];
                 im = m == 0 ? (Rr)0 : a[1];
+                if (J.scale) {
+                    // inverse Laplacian on the unit sphere: -1 / (n (n+1)), 0 at n = 0
+                    const int n = m + d;
+                    const Rr f = n == 0 ? (Rr)0 : (Rr)(-1.0 / ((double)n * (n + 1.0)));
+                    re *= f;
+                    im *= f;
+                }
             }
             tile[lane][2 * ff] = re;
             tile[lane][2 * ff + 1] = im;
@@ -257,14 +280,15 @@ __global__ void __launch_bounds__(256) k_unpack(const __grid_constant__ PackBatc
 }
 
 // dir 0: pack (spectra -> operand), 1: unpack (GEMM output -> spectra).
-st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job)
+st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job, int scale, int cp)
 {
     PackJob &J = *job;
     J.src = src;
     J.dst = dst;
     J.srow = p->srow;
     J.nspec = p->nspec;
-    J.Cp = cols_padded(nfields);
+    J.scale = scale;
+    J.Cp = cp ? cp : cols_padded(nfields);
     J.Rp = p->srow_total;
     J.ps = J.Rp * J.Cp;
     J.T = p->T;

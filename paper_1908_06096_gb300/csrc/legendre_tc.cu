@@ -476,10 +476,10 @@ static st_status make_operand_map(CUtensorMap *map, void *base, bool bf16, int C
     return ST_OK;
 }
 
-static int tc_max_nt(const st_plan *p, int dir)
+static int tc_max_nt(const st_plan *p, int set)
 {
     int mx = 16;
-    for (const auto &g : p->groups_h[dir])
+    for (const auto &g : p->groups_h[set])
         if (g.nt > mx) mx = g.nt;
     return mx;
 }
@@ -497,24 +497,25 @@ size_t tc_smem_bytes(int prec, int max_nt, int *stages_out)
     return 1024 + (size_t)S * stage + ctrl;
 }
 
-st_status tc_job(st_plan *p, int dir, int nfields, void *data, void *out, TcJob *job)
+st_status tc_job(st_plan *p, int set, int nfields, void *data, void *out, TcJob *job, int cp)
 {
     TcJob &J = *job;
-    const int C = 2 * nfields, Cp = cols_padded(nfields);
+    const int dir = set_dir(set);
+    const int C = 2 * nfields, Cp = cp ? cp : cols_padded(nfields);
     const bool bf16 = p->prec == P_BF16X3;
     const long long rows = dir == 0 ? p->srow_total : fb_rows(p);
     st_status r = make_operand_map(&J.map, data, bf16, C, rows, Cp);
     if (r != ST_OK) return r;
-    J.groups = p->groups[dir];
+    J.groups = p->groups[set];
     J.tiles = p->tiles[dir];
-    J.tab = (const char *)p->tab[dir];
+    J.tab = (const char *)p->tab[set];
     J.out = (float *)out;
     J.err = p->err;
     J.C = C;
     J.Cp = Cp;
     J.ncm = (C + TC_M - 1) / TC_M;
     J.ntiles = (long long)p->ntiles[dir] * J.ncm;
-    J.max_nt = tc_max_nt(p, dir);
+    J.max_nt = tc_max_nt(p, set);
     return ST_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <functional>
 #include <memory>
 #include <string>
 #include <vector>
@@ -174,6 +175,19 @@ __host__ __device__ inline int fft_swz_size(int L, int mode)
     return mode == 1 ? L + (L >> 4) + 1 : (mode == 2 ? L + (L >> 5) + 1 : L);
 }
 
+// Legendre table sets.  H_n^m = (1 - mu^2) dPbar_n^m/dmu has the opposite
+// parity in mu to Pbar_n^m, so the H sets exchange the Fourier-buffer halves:
+// synthesis group (m, p) writes the half 1 - p, analysis group (m, p) reads it.
+enum TableSet {
+    SET_SYN = 0,      // Pbar_n^m(mu_j)                        synthesis
+    SET_ANA = 1,      // w_j Pbar_n^m(mu_j)                    analysis
+    SET_SYN_H = 2,    // H_n^m(mu_j)                           synthesis, halves exchanged
+    SET_ANA_P1 = 3,   // w_j / (1 - mu_j^2) Pbar_n^m(mu_j)     analysis
+    SET_ANA_H1 = 4,   // w_j / (1 - mu_j^2) H_n^m(mu_j)        analysis, halves exchanged
+    NSETS = 5
+};
+inline int set_dir(int set) { return (set == SET_SYN || set == SET_SYN_H) ? 0 : 1; }
+
 struct LegGroup {
     int m, p;
     int ncol;                 // valid columns of the table
@@ -222,6 +236,8 @@ struct FftJob {
     int plan;                 // fast plan id (ST_FF_PLANS)
     int smode;                // storage mode of the direct output (fast kernels)
     int smem;                 // dynamic shared memory one CTA of this job needs (bytes)
+    int a_top;                // inverse: the odd half at m = T holds data (derivative syntheses);
+                              // otherwise no GEMM writes it (no n = T + 1) and it reads as zero
 };
 template <int MAXJ>
 struct FftBatch {
@@ -237,6 +253,7 @@ struct PackJob {
     const long long *srow;
     long long nspec, Rp, ps;
     int T, max_m, nfields, Cp, nft, nm;  // nft field tiles of 32, nm wavenumbers launched
+    int scale;                           // pack: 1 multiplies a_n^m by -1 / (n (n+1)) (0 at n = 0)
 };
 template <int MAXJ>
 struct PackBatch {
@@ -296,13 +313,20 @@ struct st_plan {
     int max_chirp = 0;                   // largest N among Bluestein rows
     int nfast = 0;                       // rows on the fast kernels: entries 0 .. nfast-1 of rowpairs
 
-    // Legendre data, [0] inverse, [1] direct
-    void *tab[2] = {nullptr, nullptr};
-    size_t tab_bytes[2] = {0, 0};
-    st::LegGroup *groups[2] = {nullptr, nullptr};
-    std::vector<st::LegGroup> groups_h[2];
+    // Legendre table sets (see st::TableSet): [0] Pbar synthesis, [1] w Pbar
+    // analysis, and, once derivatives are enabled, [2] H synthesis, [3] and
+    // [4] the analysis sets of the wind transforms.  Work lists exist per
+    // direction ([0] synthesis, [1] analysis): a set has its direction's tiles.
+    void *tab[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t tab_bytes[5] = {0, 0, 0, 0, 0};
+    st::LegGroup *groups[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<st::LegGroup> groups_h[5];
     st::LegTile *tiles[2] = {nullptr, nullptr};
     int ntiles[2] = {0, 0};
+    // derivative support (st_plan_enable_derivatives): sets 2-4 and a second
+    // Fourier buffer and spectral output, owned by this plan
+    bool deriv = false;
+    void *fb2 = nullptr, *sout2 = nullptr;
 
     // workspace.  GEMM data operands live in buffers of their own that only
     // ever hold zeros (from creation) or finite values written in their own
@@ -370,7 +394,7 @@ constexpr int SIMT_TILE = 64;
 
 // Kernel kinds for launch accounting.
 enum KernelKind {
-    K_PACK = 0, K_LEG_INV, K_FFT_INV, K_FFT_DIR, K_LEG_DIR, K_UNPACK, K_EXPORT, K_TABLES, K_NKINDS
+    K_PACK = 0, K_LEG_INV, K_FFT_INV, K_FFT_DIR, K_LEG_DIR, K_UNPACK, K_EXPORT, K_TABLES, K_COMBINE, K_NKINDS
 };
 const char *kernel_name(const st_plan *p, int kind);
 
@@ -387,9 +411,13 @@ st_status launch_fftf_dir_g2(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_inv_g0(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_inv_g1(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_inv_g2(const FftJob *jobs, int n, cudaStream_t s);
-st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job);
+// scale: 0 none, 1 the inverse Laplacian -1 / (n (n+1)) (0 at n = 0);
+// cp: column stride of the operand (0: the one of nfields)
+st_status pack_job(st_plan *p, int dir, int nfields, const void *src, void *dst, PackJob *job, int scale = 0,
+                   int cp = 0);
 st_status launch_pack_jobs(int dir, int prec, const PackJob *jobs, int n, cudaStream_t s);
-st_status simt_job(st_plan *p, int dir, int nfields, const void *data, void *out, SimtJob *job, long long *blocks);
+st_status simt_job(st_plan *p, int set, int nfields, const void *data, void *out, SimtJob *job, long long *blocks,
+                   int cp = 0);
 st_status launch_simt_jobs(int prec, const SimtJob *jobs, const long long *blocks, int n, cudaStream_t s);
 // Tensor-core Legendre stage of one request (the data operand's tensor map
 // travels with it).
@@ -403,9 +431,14 @@ struct TcJob {
     long long ntiles;         // tiles[] entries x data tiles
     int ncm, C, Cp, max_nt;
 };
-st_status tc_job(st_plan *p, int dir, int nfields, void *data, void *out, TcJob *job);
+st_status tc_job(st_plan *p, int set, int nfields, void *data, void *out, TcJob *job, int cp = 0);
 st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s, int withhold = 0,
                          unsigned long long wait_ns = 2000000000ull);
+
+// ---- plan helpers (api.cu) ----
+st_status count_launch(st_plan *p, int kind, cudaStream_t s, const std::function<st_status()> &f);
+st_status plan_alloc(st_plan *p, void **ptr, size_t bytes);
+void build_groups_deriv(st_plan *p, int set);
 
 // ---- autotuner support (api.cu) ----
 st_status rebuild_legendre(st_plan *p, cudaStream_t s);
@@ -418,12 +451,23 @@ st_status launch_bluestein_setup(st_plan *p, cudaStream_t s);
 st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s);
 // The optional buffer arguments below replace the plan's own workspace
 // buffers for one call (nullptr: use the plan's).
-st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb = nullptr);
+st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb = nullptr,
+                         int a_top = 0);
 st_status launch_pack(st_plan *p, const void *spec, int nfields, cudaStream_t s, void *sop = nullptr);
 st_status launch_unpack(st_plan *p, void *spec, int nfields, cudaStream_t s);
 st_status launch_leg_simt(st_plan *p, int dir, int nfields, cudaStream_t s, void *data = nullptr,
                           void *out = nullptr);
 st_status launch_leg_tc(st_plan *p, int dir, int nfields, cudaStream_t s, void *data = nullptr, void *out = nullptr);
+// Legendre stage of table set `set` (SIMT or tensor cores by precision), data
+// and out explicit; cp as for the job builders
+st_status launch_leg_set(st_plan *p, int set, int nfields, cudaStream_t s, void *data, void *out, int cp = 0);
+st_status launch_tables_deriv(st_plan *p, cudaStream_t s);
+// Fourier-space combination of the P and H syntheses (mode 0: winds from psi,
+// chi; mode 1: d/dlambda and (1 - mu^2) d/dmu of a scalar), in place in fb
+st_status launch_deriv_combine(st_plan *p, int mode, int nfields, void *fb, const void *fb2, cudaStream_t s);
+// spectral combination of the P and H analyses into vorticity and divergence,
+// in place in sout
+st_status launch_vordiv_combine(st_plan *p, int nfields, void *sout, const void *sout2, cudaStream_t s);
 st_status launch_fourier_export(st_plan *p, int dir, int nfields, double *out, cudaStream_t s);
 st_status launch_gauss(int nlat, double *mu, double *w, cudaStream_t s);
 st_status launch_legendre_values(int T, const double *mu, int nmu, double *out, cudaStream_t s);

@@ -214,6 +214,77 @@ st_status launch_tables(st_plan *p, cudaStream_t s)
     return ST_OK;
 }
 
+// ---------------------------------------------------------------- derivative tables
+//
+// H_n^m = (1 - mu^2) dPbar_n^m/dmu = (n+1) eps_n^m Pbar_{n-1}^m - n eps_{n+1}^m Pbar_{n+1}^m,
+// eps_n^m = sqrt((n^2 - m^2) / (4 n^2 - 1)) (0 for n <= m).  One thread per
+// (m, northern row j) walks the Pbar recurrence to T + 1 and writes, for
+// n = m + p + 2k <= T:
+//   set SYN_H  (synthesis layout): H_n^m(mu_j)                      at (col j, r k)
+//   set ANA_P1 (analysis layout):  w_j / (1 - mu_j^2) Pbar_n^m(mu_j) at (col k, r j)
+//   set ANA_H1 (analysis layout):  w_j / (1 - mu_j^2) H_n^m(mu_j)    at (col k, r j)
+// (zeros on rows that do not keep m).
+__device__ inline double eps_nm(int n, int m)
+{
+    if (n <= m) return 0.0;
+    const double dn = n, dm = m;
+    return sqrt((dn * dn - dm * dm) / (4.0 * dn * dn - 1.0));
+}
+
+template <int PREC>
+__global__ void k_tables_deriv(int T, int J, int max_m, const double *mu, const double *w, const int *Mrow,
+                               const LegGroup *gh, const LegGroup *gp1, const LegGroup *gh1, void *tab_h,
+                               void *tab_p1, void *tab_h1)
+{
+    int m = blockIdx.y;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J || m > max_m) return;
+    const bool keep = m <= Mrow[j];
+    const double x = mu[j], c = w[j] / ((1.0 - x) * (1.0 + x));
+    const LegGroup g0[2] = {gh[2 * m], gh[2 * m + 1]};
+    const LegGroup g1[2] = {gp1[2 * m], gp1[2 * m + 1]};
+    const LegGroup g2[2] = {gh1[2 * m], gh1[2 * m + 1]};
+    double pa = 0.0, pb = 0.0;  // Pbar_{n-2}, Pbar_{n-1}
+    pbar_column(T + 1, m, x, [&](int n, double v) {
+        // v = Pbar_n: now H_{n-1} is known
+        const int nn = n - 1;
+        if (nn >= m) {
+            double h = (nn + 1.0) * eps_nm(nn, m) * pa - (double)nn * eps_nm(nn + 1, m) * v;
+            double pv = pb;
+            if (!keep) h = pv = 0.0;
+            const int p = (nn - m) & 1, k = (nn - m) >> 1;
+            if (g0[p].K > 0) put_table<PREC>(tab_h, g0[p], j, k, h);
+            if (g1[p].ncol > 0) put_table<PREC>(tab_p1, g1[p], k, j, c * pv);
+            if (g2[p].ncol > 0) put_table<PREC>(tab_h1, g2[p], k, j, c * h);
+        }
+        pa = pb;
+        pb = v;
+    });
+}
+
+st_status launch_tables_deriv(st_plan *p, cudaStream_t s)
+{
+    int *Mrow_d = nullptr;
+    ST_CUDA(cudaMallocAsync(&Mrow_d, sizeof(int) * p->J, s));
+    ST_CUDA(cudaMemcpyAsync(Mrow_d, p->Mrow.data(), sizeof(int) * p->J, cudaMemcpyHostToDevice, s));
+    dim3 grid((p->J + 63) / 64, p->max_m + 1);
+#define ST_TD(PR)                                                                                              \
+    k_tables_deriv<PR><<<grid, 64, 0, s>>>(p->T, p->J, p->max_m, p->mu, p->w, Mrow_d, p->groups[SET_SYN_H],  \
+                                           p->groups[SET_ANA_P1], p->groups[SET_ANA_H1], p->tab[SET_SYN_H],    \
+                                           p->tab[SET_ANA_P1], p->tab[SET_ANA_H1])
+    switch (p->prec) {
+    case P_FP64: ST_TD(P_FP64); break;
+    case P_FP32: ST_TD(P_FP32); break;
+    case P_TF32X3: ST_TD(P_TF32X3); break;
+    default: ST_TD(P_BF16X3); break;
+    }
+#undef ST_TD
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(Mrow_d, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_tables_deriv");
+    return ST_OK;
+}
+
 // ---------------------------------------------------------------- FFT roots
 
 template <typename C>

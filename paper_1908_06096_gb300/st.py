@@ -86,6 +86,10 @@ SIGNATURES = {
     "st_batch_destroy": [_VP],
     "st_static_scratch_bytes": [],
     "st_build_info": [ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "st_plan_enable_derivatives": [_VP, _VP],
+    "st_inv_trans_deriv": [_VP, _VP, _VP, _I, _VP],
+    "st_inv_trans_uv": [_VP, _VP, _VP, _I, _VP],
+    "st_dir_trans_vordiv": [_VP, _VP, _VP, _I, _VP],
 }
 
 
@@ -257,6 +261,35 @@ class Plan:
             out = torch.empty((nf, self.nspec, 2), dtype=self.dtype, device=grid.device)
         _check(load().st_dir_trans(self._h, _ptr(grid), _ptr(out), nf, _stream_handle(stream)), "st_dir_trans")
         return out
+
+    # -- derivative and wind transforms (unit sphere; U = u cos(phi), V = v cos(phi))
+    def enable_derivatives(self, stream=None):
+        _check(load().st_plan_enable_derivatives(self._h, _stream_handle(stream)), "st_plan_enable_derivatives")
+
+    def inv_deriv(self, spec: torch.Tensor, stream=None):
+        """(dF/dlambda, cos(phi) dF/dphi), each [nfields, grid_points]."""
+        nf = self._nf(spec, self.nspec * 2)
+        out = torch.empty((2 * nf, self.npts), dtype=self.dtype, device=spec.device)
+        _check(load().st_inv_trans_deriv(self._h, _ptr(spec), _ptr(out), nf, _stream_handle(stream)),
+               "st_inv_trans_deriv")
+        return out[:nf], out[nf:]
+
+    def inv_uv(self, vor: torch.Tensor, div: torch.Tensor, stream=None):
+        """Wind images (U, V), each [nfields, grid_points], from vorticity and divergence spectra."""
+        nf = self._nf(vor, self.nspec * 2)
+        vd = torch.cat([vor.reshape(nf, self.nspec, 2), div.reshape(nf, self.nspec, 2)]).contiguous()
+        out = torch.empty((2 * nf, self.npts), dtype=self.dtype, device=vor.device)
+        _check(load().st_inv_trans_uv(self._h, _ptr(vd), _ptr(out), nf, _stream_handle(stream)), "st_inv_trans_uv")
+        return out[:nf], out[nf:]
+
+    def dir_vordiv(self, U: torch.Tensor, V: torch.Tensor, stream=None):
+        """(vorticity, divergence) spectra [nfields, nspec, 2] from wind images U, V."""
+        nf = self._nf(U, self.npts)
+        uv = torch.cat([U.reshape(nf, self.npts), V.reshape(nf, self.npts)]).contiguous()
+        out = torch.empty((2 * nf, self.nspec, 2), dtype=self.dtype, device=U.device)
+        _check(load().st_dir_trans_vordiv(self._h, _ptr(uv), _ptr(out), nf, _stream_handle(stream)),
+               "st_dir_trans_vordiv")
+        return out[:nf], out[nf:]
 
     def autotune(self, nfields: int | None = None, cache_path: str | None = None, stream=None):
         """Time candidate launch shapes on this plan and keep the fastest
