@@ -174,21 +174,23 @@ st_status st_dir_trans(st_plan_t plan, const void *grid_dev, void *spec_dev, int
  * spectral operand and the Fourier buffer) lives in one fixed array compiled
  * into the library (st_static_scratch_bytes() bytes, 32 MiB) instead of the
  * plan's workspace.  The paper has no counterpart: it is for callers that
- * must not allocate device memory where they run the transform -- work
- * recorded during a global-mode stream capture, real-time loops where an
- * allocation may stall, frameworks that own all device memory -- and it calls
- * no cudaMalloc, cudaFree or other allocating routine.
+ * cannot allocate device memory where they run the transform -- real-time
+ * loops where an allocation may stall, frameworks that own all device memory
+ * through their own allocator -- and it calls no cudaMalloc, cudaFree or
+ * other allocating routine.
  *  - Returns ST_ERR_ARG (message in st_last_error) when the plan and
  *    `nfields` need more scratch than the array holds; nfields may exceed the
  *    plan's max_fields as long as the scratch suffices.
  *  - The first call on each device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    life of the process; make that first call before any stream capture,
+ *    and do not call the entry point on a device after cudaDeviceReset.
  *  - Every call on a device shares the one array and it keeps the last
  *    call's contents; the call clears what must start at zero itself.  Calls
  *    that can overlap on the GPU (other streams, or the same array used from
  *    several host threads without ordering) race on it and give wrong results.
  *  - Every GPU that loads the library holds the array until the process exits.
+ *  - Its launches are counted and timed with the plan's (st_plan_timings).
  */
 st_status st_inv_trans_static(st_plan_t plan, const void *spec_dev, void *grid_dev, int nfields,
                               void *stream);
@@ -228,6 +230,24 @@ st_status st_inv_trans_uv(st_plan_t plan, const void *vordiv_dev, void *uv_dev, 
  *   D_n^m    = sum_j w_j / (1 - mu_j^2) (i m U_m Pbar_n^m - V_m H_n^m),
  * U_m, V_m the rows' Fourier coefficients (1/N_j sum_k e^{-i m lambda_k}). */
 st_status st_dir_trans_vordiv(st_plan_t plan, const void *uv_dev, void *vordiv_dev, int nfields, void *stream);
+
+/*
+ * On-disk table cache (not in the paper; the restart analogue of the SH
+ * dwarf's once-per-run set-up).  st_plan_save_tables writes the plan's
+ * Gaussian nodes and weights and both Legendre table sets, exactly as they
+ * sit on the device, to `path`, with a header naming the truncation, grid,
+ * precision and table layout and a checksum of the contents.
+ * st_plan_load_tables reads such a file into a plan created with the same
+ * truncation, grid, precision and layout: ST_ERR_ARG (message in
+ * st_last_error) if the header does not match or the checksum fails -- the
+ * plan's tables are then untouched -- and ST_ERR_BUSY if the plan shares its
+ * tables with another plan.  Both are synchronous.  When the environment
+ * variable ST_TABLE_CACHE names a directory, st_plan_create loads a plan's
+ * tables from a matching file there instead of building them, and writes
+ * one after building them.
+ */
+st_status st_plan_save_tables(st_plan_t plan, const char *path);
+st_status st_plan_load_tables(st_plan_t plan, const char *path);
 
 /* Size in bytes of the array st_inv_trans_static uses. */
 size_t st_static_scratch_bytes(void);

@@ -589,7 +589,24 @@ static st_status plan_build(st_plan *p, cudaStream_t s)
         ST_CUDA(cudaMemsetAsync(p->tab[dir], 0, std::max<size_t>(p->tab_bytes[dir], 16), s));
         p->table_bytes += p->tab_bytes[dir];
     }
-    if ((r = launch_tables(p, s))) return r;
+    // tables from the on-disk cache (directory in ST_TABLE_CACHE) when it holds
+    // this plan's, else built here and written there
+    const char *cache_dir = getenv("ST_TABLE_CACHE");
+    bool cached = false;
+    if (cache_dir && *cache_dir) {
+        ST_CUDA(cudaStreamSynchronize(s));
+        cached = load_tables(p, table_cache_path(p, cache_dir).c_str()) == ST_OK;
+        set_last_error("");
+    }
+    if (!cached) {
+        if ((r = launch_tables(p, s))) return r;
+        p->launches[K_TABLES]++;
+        if (cache_dir && *cache_dir) {
+            ST_CUDA(cudaStreamSynchronize(s));
+            save_tables(p, table_cache_path(p, cache_dir).c_str());  // best effort
+            set_last_error("");
+        }
+    }
 
     // the read-only arrays now belong to a shareable core
     {

@@ -440,6 +440,11 @@ st_status count_launch(st_plan *p, int kind, cudaStream_t s, const std::function
 st_status plan_alloc(st_plan *p, void **ptr, size_t bytes);
 void build_groups_deriv(st_plan *p, int set);
 
+// ---- on-disk table cache (cache.cu) ----
+std::string table_cache_path(const st_plan *p, const char *dir);
+st_status save_tables(st_plan *p, const char *path);
+st_status load_tables(st_plan *p, const char *path);
+
 // ---- autotuner support (api.cu) ----
 st_status rebuild_legendre(st_plan *p, cudaStream_t s);
 std::string tune_key(const st_plan *p, int nfields);

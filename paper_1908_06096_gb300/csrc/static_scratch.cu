@@ -1,14 +1,13 @@
 // st_inv_trans_static: the inverse transform with its scratch in a fixed,
 // file-scope device array instead of the plan's workspace.
 //
-// Who needs it: code that must not allocate device memory at the point where
-// it runs the transform -- for example work recorded while a CUDA stream is
-// being captured in global capture mode (cudaMalloc is refused there), hard
-// real-time loops where an allocation could stall, or host frameworks that own
-// all device memory through their own allocator and do not let components call
-// cudaMalloc or cudaFree.  This entry point calls neither, nor any other
-// allocating routine; the scratch it needs (the packed spectral operand and the
-// Fourier buffer) comes from g_static_scratch below.
+// Who needs it: code that cannot allocate device memory at the point where it
+// runs the transform -- hard real-time loops where an allocation could stall,
+// or host frameworks that own all device memory through their own allocator
+// and do not let components call cudaMalloc or cudaFree.  This entry point
+// calls neither, nor any other allocating routine; the scratch it needs (the
+// packed spectral operand and the Fourier buffer) comes from g_static_scratch
+// below.
 #include "st_internal.cuh"
 
 #include <mutex>
@@ -21,9 +20,10 @@ namespace {
 constexpr size_t ST_STATIC_SCRATCH_BYTES = 32u << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_static_scratch[ST_STATIC_SCRATCH_BYTES];
 
-// Device address of g_static_scratch, looked up once per device (the name
-// g_static_scratch is only a host-side stand-in in host code; giving it to a
-// kernel would hand the kernel the wrong memory).
+// Device address of g_static_scratch, looked up once per device and kept for
+// the life of the process (the name g_static_scratch is only a host-side
+// stand-in in host code; giving it to a kernel would hand the kernel the
+// wrong memory).
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void *g_scratch_ptr[kMaxDevices] = {nullptr};
@@ -82,10 +82,13 @@ extern "C" st_status st_inv_trans_static(st_plan_t p, const void *spec_dev, void
     // operand region is cleared first.  The Fourier-buffer region needs no
     // clearing: the FFT reads only entries this call writes.
     ST_CUDA(cudaMemsetAsync(sop, 0, sop_bytes, s));
-    if ((r = launch_pack(p, spec_dev, nfields, s, sop))) return r;
-    r = prec_is_tc(p->prec) ? launch_leg_tc(p, 0, nfields, s, sop, fb) : launch_leg_simt(p, 0, nfields, s, sop, fb);
+    // counted and timed with the plan's other launches
+    if ((r = count_launch(p, K_PACK, s, [&] { return launch_pack(p, spec_dev, nfields, s, sop); }))) return r;
+    r = count_launch(p, K_LEG_INV, s, [&] {
+        return prec_is_tc(p->prec) ? launch_leg_tc(p, 0, nfields, s, sop, fb) : launch_leg_simt(p, 0, nfields, s, sop, fb);
+    });
     if (r) return r;
-    return launch_fft_inv(p, grid_dev, nfields, s, fb);
+    return count_launch(p, K_FFT_INV, s, [&] { return launch_fft_inv(p, grid_dev, nfields, s, fb); });
 }
 
 extern "C" size_t st_static_scratch_bytes(void) { return ST_STATIC_SCRATCH_BYTES; }

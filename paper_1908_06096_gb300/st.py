@@ -86,6 +86,8 @@ SIGNATURES = {
     "st_batch_destroy": [_VP],
     "st_static_scratch_bytes": [],
     "st_build_info": [ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "st_plan_save_tables": [_VP, ctypes.c_char_p],
+    "st_plan_load_tables": [_VP, ctypes.c_char_p],
     "st_plan_enable_derivatives": [_VP, _VP],
     "st_inv_trans_deriv": [_VP, _VP, _VP, _I, _VP],
     "st_inv_trans_uv": [_VP, _VP, _VP, _I, _VP],
@@ -261,6 +263,12 @@ class Plan:
             out = torch.empty((nf, self.nspec, 2), dtype=self.dtype, device=grid.device)
         _check(load().st_dir_trans(self._h, _ptr(grid), _ptr(out), nf, _stream_handle(stream)), "st_dir_trans")
         return out
+
+    def save_tables(self, path: str):
+        _check(load().st_plan_save_tables(self._h, path.encode()), "st_plan_save_tables")
+
+    def load_tables(self, path: str):
+        _check(load().st_plan_load_tables(self._h, path.encode()), "st_plan_load_tables")
 
     # -- derivative and wind transforms (unit sphere; U = u cos(phi), V = v cos(phi))
     def enable_derivatives(self, stream=None):

@@ -1,13 +1,14 @@
-"""st_inv_trans_static: the inverse transform for callers that must not
-allocate device memory where they run it (work recorded during a global-mode
-stream capture, real-time loops, frameworks that own all device memory).  Its
-scratch is a fixed array inside the library instead of the plan's workspace.
+"""st_inv_trans_static: the inverse transform for callers that cannot
+allocate device memory where they run it (real-time loops where an
+allocation may stall, frameworks that own all device memory).  Its scratch is
+a fixed array inside the library instead of the plan's workspace.
 
 Checked here through the C ABI: two calls in a row agree with st_inv_trans
 (within the split-precision tolerance the other parity tests use), a call
 after another plan with a different layout and precision has used the array
-still agrees, and a request too large for the array is refused.  This file is
-collected last on purpose.
+still agrees, more fields than the plan's max_fields work while the array
+holds them, the launches are counted with the plan's, and a request too
+large for the array is refused.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -85,3 +86,24 @@ def test_static_scratch_rejects_oversize(st_mod):
     assert rc == 1  # ST_ERR_ARG
     assert b"static scratch" in lib.st_last_error()
     plan.close()
+
+
+def test_static_scratch_beyond_max_fields_and_counted(st_mod):
+    """nfields above the plan's max_fields (the array, not the plan's
+    workspace, bounds the static call) agrees with a plan sized for them; the
+    call's three launches are counted with the plan's."""
+    small = st_mod.Plan(31, "regular", precision="bf16x3", max_fields=2)
+    big = st_mod.Plan(31, "regular", precision="bf16x3", max_fields=5)
+    spec = _spec(31, 5, 31, torch.float32)
+    ref = big.inv(spec).clone()
+    small.reset_timings()
+    out = torch.full_like(ref, float("nan"))
+    rc = _static_call(st_mod, small, spec, out)
+    assert rc == 0, st_mod.load().st_last_error()
+    torch.cuda.synchronize()
+    assert max_rel(out.double().cpu().numpy(), ref.double().cpu().numpy()) <= TOL["bf16x3"]
+    counts = {k: v["launches"] for k, v in small.timings().items()}
+    assert counts.get("pack_spectra") == 1 and counts.get("fft_inverse") == 1
+    assert counts.get("legendre_inverse_tcgen05") == 1
+    small.close()
+    big.close()
