@@ -35,6 +35,7 @@ WORKLOADS = {
     "t639_o640_548": (639, "octahedral", 1280, 0, 548, 1.5, 1002),
     "t159_reg_411": (159, "regular", 160, 320, 411, 1.0, 1001),
     "t639_o640_64": (639, "octahedral", 1280, 0, 64, 1.5, 1002),
+    "t639_o640_256": (639, "octahedral", 1280, 0, 256, 1.5, 1002),
     "t31_reg_10": (31, "regular", 32, 64, 10, 1.0, 1000),
     # the operational resolution of the paper's test cases: TCO1279 on O1280
     # (2560 Gaussian latitudes, rows 20 + 4i up to 5140 points), 137 levels
@@ -122,6 +123,32 @@ def geometry(rows, T):
     return J, M, max_m, j0
 
 
+# FFT lengths of the library's compile-time FP32 plans (ST_FF_PLANS): a row of
+# N points runs one FFT of length N when N is one of them, else Bluestein with
+# two FFTs of the shortest length >= N + 2M.  FP64 plans use 5-smooth lengths.
+FF_LENGTHS = [16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512, 640, 768, 1024, 1280,
+              1536, 2048, 2560, 3072, 4096, 5120, 6144, 8192]
+
+
+def fft_flops(rows, T, F, prec):
+    """FP32 flops of one FFT stage (one direction) as the library runs it,
+    5 L log2 L per complex FFT of length L, row pairs as complex sequences."""
+    import math
+    J = len(rows) // 2
+    tot = 0.0
+    for j in range(J):
+        N = int(rows[j])
+        M = min(T, (N - 1) // 2)
+        if N in FF_LENGTHS:
+            tot += 5.0 * N * math.log2(N)
+        else:
+            L = min((x for x in FF_LENGTHS if x >= N + 2 * M), default=None)
+            if L is None:
+                return None
+            tot += 2 * 5.0 * L * math.log2(L) + 6.0 * L
+    return tot * F if prec != "fp64" else None
+
+
 def algorithmic(T, rows, F, prec):
     """Algorithmic work of one launch of each kernel for F fields (the counts
     the roofline fractions divide by)."""
@@ -138,7 +165,12 @@ def algorithmic(T, rows, F, prec):
     fb_vals = sum(M[j] + 1 for j in range(J)) * 2 * 2 * F  # (E,O or S,A) x (re,im)
     el = 8 if prec == "fp64" else 4
     op = {"bf16x3": 4, "tf32x3": 8, "fp32": 4, "fp64": 8}[prec]
+    # Legendre HBM bytes per direction: its tables (about half the plan's), the
+    # operand read and the output written (row-trimmed Fourier-buffer values)
     return {
+        "leg_inv_bytes": nspec * 2 * F * op + fb_vals * el,
+        "leg_dir_bytes": fb_vals * op + nspec * 2 * F * el,
+        "fft_flops": fft_flops(rows, T, F, prec),
         "leg_flops": flops, "leg_tensor_flops": flops * split,
         "fft_dir_bytes": npts * F * el + fb_vals * op,
         "fft_inv_bytes": fb_vals * el + npts * F * el,
@@ -234,6 +266,7 @@ def config_of(wl, prec):
     desc = {"t639_o640_548": "T639 octahedral O640 (1280 Gaussian latitudes, rows 20+4i), 137 levels x 4 fields",
             "t159_reg_411": "T159 regular 160 x 320 Gaussian grid, 137 levels x 3 fields",
             "t639_o640_64": "T639 octahedral O640, 64 fields (profiling case)",
+            "t639_o640_256": "T639 octahedral O640, 256 fields (profiling case of the Legendre GEMM)",
             "t31_reg_10": "T31 regular 32 x 64 Gaussian grid, 10 fields",
             "t1279_o1280_137": "T1279 octahedral O1280 (2560 Gaussian latitudes, rows 20+4i), 137 levels x 1 field"}[wl]
     return {"workload": desc, "T": T, "grid": grid, "nlat": nlat, "nlon": nlon or None, "fields": F,
@@ -301,6 +334,10 @@ def run_ours(args, ws, rank, local):
     rows = plan.row_lengths()
     alg = algorithmic(T, rows, F, prec)
     tensor_peak = pk["bf16_tflops_sustained"] * (0.5 if prec == "tf32x3" else 1.0)
+    # FP32 pipe: 128 FMA lanes x 2 flops per SM per clock at the maximum SM clock
+    props = torch.cuda.get_device_properties(local)
+    fp32_peak = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    tab_dir = plan.info.table_bytes / 2.0
     kern = {}
     total_k = sum(v["total_ms"] for v in ktimes.values()) or 1.0
     for name, v in ktimes.items():
@@ -318,6 +355,24 @@ def run_ours(args, ws, rank, local):
                 e.update(bound="hbm", unit="GB/s", achieved=alg[key] / (per * 1e-3) / 1e9, peak=pk["hbm_gbs"])
         if e.get("peak"):
             e["frac"] = e["achieved"] / e["peak"]
+        # the other side of each kernel's roofline, and which one binds
+        if name.startswith("legendre"):
+            b = tab_dir + alg["leg_inv_bytes" if "inverse" in name else "leg_dir_bytes"]
+            e["hbm"] = {"bytes": b, "achieved_gbs": b / (per * 1e-3) / 1e9,
+                        "frac": b / (per * 1e-3) / 1e9 / pk["hbm_gbs"]}
+            t_hbm = b / (pk["hbm_gbs"] * 1e9)
+            t_ten = alg["leg_tensor_flops"] / (tensor_peak * 1e12) if e.get("bound") == "tensor" else 0.0
+            e["binding"] = "hbm" if t_hbm > t_ten else e.get("bound")
+            e["frac_of_binding_bound"] = max(t_hbm, t_ten) / (per * 1e-3)
+        if name.startswith("fft") and alg.get("fft_flops"):
+            e["fp32_pipe"] = {"flops": alg["fft_flops"], "achieved_tflops": alg["fft_flops"] / (per * 1e-3) / 1e12,
+                              "peak_tflops": fp32_peak,
+                              "frac": alg["fft_flops"] / (per * 1e-3) / 1e12 / fp32_peak,
+                              "model": "5 L log2 L flops per complex FFT of length L as run (Bluestein: two)"}
+            t_alu = alg["fft_flops"] / (fp32_peak * 1e12)
+            t_hbm = alg[key] / (pk["hbm_gbs"] * 1e9)
+            e["binding"] = "alu" if t_alu > t_hbm else "hbm"
+            e["frac_of_binding_bound"] = max(t_alu, t_hbm) / (per * 1e-3)
         kern[name] = e
     dom = max(kern, key=lambda k: kern[k]["share"])
     d = kern[dom]
