@@ -62,6 +62,7 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
     base.T = p->T;
     base.Jp = p->Jp;
     base.smode = store_of(p->prec);
+    base.err = p->err;
 
     // fast rows
     const size_t budget = (size_t)p->fft_kb[dir] * 1024;

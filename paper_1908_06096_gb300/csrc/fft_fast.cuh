@@ -243,6 +243,62 @@ __device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// ---- bulk copies (TMA engine) into shared memory, completion on an mbarrier.
+// Every wait is bounded: past FF_WAIT_NS the CTA records bit 8 in the plan's
+// error word, drains its copies (again bounded) and gives up the row.
+constexpr unsigned long long FF_WAIT_NS = 2000000000ull;  // 2 s; a legitimate wait takes microseconds
+constexpr int FF_ERR_WAIT = 8;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// true once phase `parity` of the barrier completed; false when it did not
+// within FF_WAIT_NS or another thread of the CTA gave up (*abort set)
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    if (bar_test(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    while (!bar_test(bar, parity)) {
+        if (*abort) return false;
+        if (gtime() - t0 > FF_WAIT_NS) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// One thread: set the barrier up for `bytes` of copies and arrive.
+__device__ __forceinline__ void bar_init_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // ---- plans
 template <int A, int B, int Cc = 1, int D = 1>
 struct Plan {
@@ -382,6 +438,44 @@ __device__ __forceinline__ void stage1_in(C *x, int G, const C *__restrict__ tw,
     }
 }
 
+// Element of field f's slot where its raw rows are staged: the slot start
+// rounded up to an even element, so 16-byte aligned; the N + N floats end
+// inside the slot because N + 1 <= SL.
+__device__ __forceinline__ int raw_at(int f, int SL) { return (f * SL + 1) & ~1; }
+
+// Stage 1 of the DIF on rows staged raw in shared memory: field f's north
+// row (N floats) then south row sit at element raw_at(f, SL) of its own
+// slot.  One item per thread per field (L / R1 <= NT); each field's raw
+// values are read by every thread before any thread overwrites the slot.
+// cz holds the thread's R1 chirp factors (ones on mode-0 rows), loaded once
+// for all fields.
+template <class PL>
+__device__ __forceinline__ void stage1_raw(C *x, int G, const C *__restrict__ tw, int N, const C *cz)
+{
+    constexpr int L = PL::L, R = PL::template R<1>(), ST = L / R, SL = PL::SL;
+    static_assert(ST <= NT, "one stage-1 item per thread per field");
+    const int n = threadIdx.x;
+    for (int f = 0; f < G; ++f) {
+        const float *raw = (const float *)(x + raw_at(f, SL));
+        C v[R];
+        if (n < ST) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int e = n + q * ST;
+                v[q] = e < N ? cmul(cz[q], make_float2(raw[e], raw[N + e])) : make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        if (n < ST) {
+            dft<R>(v);
+            twiddle_pow<R>(v, tw[n]);
+            C *xf = x + f * SL;
+#pragma unroll
+            for (int q = 0; q < R; ++q) xf[slot_of<ST, R>(n, q)] = v[q];
+        }
+    }
+}
+
 // Stage 1 of the DIT (natural order out), handing output e of field f to
 // out(f, e, value).
 // pre(e) is read for every output before the pass's shared-memory loads (a
@@ -493,15 +587,62 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
     const long long npts = J.npts;
     const long long on = rp.off_n, os = rp.off_s;
 
-    stage1_in<PL>(x, G, twg, [&](int f, int e, int) -> C {
-        C z = make_float2(0.f, 0.f);
-        if (e < N) {
-            const float *g = grid + f * npts;
-            z = make_float2(__ldg(g + on + e), __ldg(g + os + e));
-            if (blue) z = cmul(z, __ldg(&chirp[e]));
+    // Rows whose offsets, length and field stride are multiples of four
+    // floats arrive by bulk copies into the fields' slots (one per row and
+    // field, tracked by one barrier) instead of per-thread loads.
+    constexpr bool kRawFits = PL::L / PL::template R<1>() <= NT;
+    const bool raw = kRawFits && G > 0 && ((on | os | (long long)N | npts) & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(J.src) & 15) == 0 && (smem_addr(x) & 15) == 0;
+    if (raw) {
+        __shared__ __align__(8) unsigned long long rbar;
+        __shared__ int abort_raw;
+        const uint32_t bar = smem_addr(&rbar);
+        if (threadIdx.x == 0) {
+            abort_raw = 0;
+            bar_init_expect(bar, (uint32_t)(G * 8 * N));
+            for (int f = 0; f < G; ++f) {
+                float *d = (float *)(x + raw_at(f, SL));
+                bulk_copy(d, grid + f * npts + on, 4u * N, bar);
+                bulk_copy(d + N, grid + f * npts + os, 4u * N, bar);
+            }
         }
-        return z;
-    });
+        __syncthreads();
+        // the chirp factors of this thread's stage-1 elements, loaded while
+        // the rows are in flight
+        constexpr int R1 = PL::template R<1>(), ST1 = PL::L / R1;
+        C cz[R1];
+#pragma unroll
+        for (int q = 0; q < R1; ++q) {
+            const int e = threadIdx.x + q * ST1;
+            cz[q] = make_float2(1.f, 0.f);
+            if (blue && threadIdx.x < ST1 && e < N) cz[q] = __ldg(&chirp[e]);
+        }
+        cp_async_wait_all();
+        bar_wait(bar, 0, &abort_raw);
+        __syncthreads();
+        if (abort_raw) {
+            // give the copies in flight a bounded chance to land before the
+            // shared memory is released
+            if (threadIdx.x == 0) {
+                atomicOr(J.err, FF_ERR_WAIT);
+                const unsigned long long t0 = gtime();
+                while (!bar_test(bar, 0) && gtime() - t0 < FF_WAIT_NS) {
+                }
+            }
+            return;
+        }
+        if constexpr (kRawFits) stage1_raw<PL>(x, G, tw, N, cz);
+    } else {
+        stage1_in<PL>(x, G, twg, [&](int f, int e, int) -> C {
+            C z = make_float2(0.f, 0.f);
+            if (e < N) {
+                const float *g = grid + f * npts;
+                z = make_float2(__ldg(g + on + e), __ldg(g + os + e));
+                if (blue) z = cmul(z, __ldg(&chirp[e]));
+            }
+            return z;
+        });
+    }
     cp_async_wait_all();
     __syncthreads();
     middle_stages<PL, false>(x, G, tw);

@@ -1,6 +1,7 @@
 // Fast FP32 row FFTs, direct direction, plan group 0 (fft_fast_inst.cuh).
-// the direct runs best at 80 registers a thread (3 CTAs per SM)
-#define FF_MINB 3
+// the direct runs best at 128 registers a thread (2 CTAs per SM) since its rows
+// arrive by bulk copies
+#define FF_MINB 2
 #define FF_DIR 1
 #define FF_GROUP 0
 #define FF_KERNEL k_fftf_dir_g0

@@ -238,6 +238,7 @@ struct FftJob {
     int smem;                 // dynamic shared memory one CTA of this job needs (bytes)
     int a_top;                // inverse: the odd half at m = T holds data (derivative syntheses);
                               // otherwise no GEMM writes it (no n = T + 1) and it reads as zero
+    int *err;                 // the plan's device error word (bounded waits set bit 8 on expiry)
 };
 template <int MAXJ>
 struct FftBatch {
