@@ -371,12 +371,12 @@ __device__ __forceinline__ void stage(C *x, int G, const C *__restrict__ tw, con
         C *xf = x + f * SL;
         const int e0 = b * NS + n1;
         C v[R];
-        float4 kq[KERN ? R / 2 : 1];
+        C kq[KERN ? R : 1];
         if constexpr (KERN) {
-            // the R kernel-spectrum values of this block are contiguous in
-            // global memory (16-byte aligned: R and the row offsets are even)
+            // value q of block b of the kernel spectrum sits at q NB + b
+            // (consecutive threads, consecutive blocks: coalesced)
 #pragma unroll
-            for (int q = 0; q < R / 2; ++q) kq[q] = __ldg((const float4 *)(kern + e0) + q);
+            for (int q = 0; q < R; ++q) kq[q] = __ldg(&kern[q * NB + b]);
         }
 #pragma unroll
         for (int q = 0; q < R; ++q) v[q] = xf[slot_of<ST, R>(e0, q)];
@@ -384,10 +384,7 @@ __device__ __forceinline__ void stage(C *x, int G, const C *__restrict__ tw, con
             // ST == 1 here: no twiddles on either side of the product
             dft<R>(v);
 #pragma unroll
-            for (int q = 0; q < R / 2; ++q) {
-                v[2 * q] = cconj(cmul(v[2 * q], make_float2(kq[q].x, kq[q].y)));
-                v[2 * q + 1] = cconj(cmul(v[2 * q + 1], make_float2(kq[q].z, kq[q].w)));
-            }
+            for (int q = 0; q < R; ++q) v[q] = cconj(cmul(v[q], kq[q]));
             dft<R>(v);
         } else if constexpr (ST == 1) {
             dft<R>(v);

@@ -393,18 +393,24 @@ __global__ void k_bluestein_kern(const RowPair *rps, int J, double2 *scratch, lo
         y = t;
         Lc *= R;
     }
-    // stored in the digit-reversed order the runtime DIF passes leave their
-    // output in, so the pointwise product needs no permutation
+    // stored in the digit-reversed order the DIF passes leave their output
+    // in, so the pointwise product needs no permutation.  Rows of the
+    // compile-time plans transpose each block of R (the last radix) places:
+    // place b R + q sits at q (L / R) + b, so that the threads of the fused
+    // product pass, one block each, read consecutive values.
     const double inv = 1.0 / (double)L;
+    const int RP = r.rad[r.nrad - 1], NBP = L / RP;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         const double2 vd = x[i], vi = x[i == 0 ? 0 : L - i];
+        int pos = dif_pos(i, r);
+        if (r.fast >= 0) pos = (pos % RP) * NBP + pos / RP;
         C v;
         v.x = (decltype(v.x))(vd.x * inv);
         v.y = (decltype(v.y))(vd.y * inv);
-        kern[r.kern_off + dif_pos(i, r)] = v;
+        kern[r.kern_off + pos] = v;
         v.x = (decltype(v.x))(vi.x * inv);
         v.y = (decltype(v.y))(vi.y * inv);
-        kern[nkern + r.kern_off + dif_pos(i, r)] = v;
+        kern[nkern + r.kern_off + pos] = v;
     }
 }
 
