@@ -780,7 +780,8 @@ st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int pr
     p->nlon = grid->kind == ST_GRID_REGULAR ? grid->nlon : 0;
     p->prec = prec;
     p->max_fields = max_fields;
-    if (prec != ST_FP64) p->fft_kb[0] = p->fft_kb[1] = 72;  // fast kernels: 3 CTAs per SM
+    // fast kernels: two CTAs of 256 threads per SM (128 registers a thread)
+    if (prec != ST_FP64) p->fft_kb[0] = p->fft_kb[1] = 108;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaGetDevice"); }
     cudaDeviceProp prop;
