@@ -518,8 +518,9 @@ def run_ours(args, ws, rank, local):
 def mixed_batch(args, dev):
     """The 48-request mixed batch: T uniform over {79,159,255,319,511,639},
     regular (T+1) x (2T+2) or octahedral O(T+1) grids, 1-256 fields each,
-    BF16x3; one round trip per request, all requests in one batch (one launch
-    per stage, replayed from a CUDA graph)."""
+    BF16x3; one round trip per request, all requests in one batch: timed as
+    one persistent launch and as one launch per stage replayed from a CUDA
+    graph (the two must agree bit for bit)."""
     import torch
 
     from paper_1908_06096_gb300 import inputs, st
@@ -535,17 +536,30 @@ def mixed_batch(args, dev):
         items.append((p, "round", spec, g, out))
         fields += r["nfields"]
     batch = st.Batch(items)
-    for _ in range(max(3, args.warmup)):
-        batch.run(graph=True)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n = max(3, args.steps)
-    e0.record()
-    for _ in range(n):
-        batch.run(graph=True)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / n
+
+    def timed(**kw):
+        for _ in range(max(3, args.warmup)):
+            batch.run(**kw)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n):
+            batch.run(**kw)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    ms_graph = timed(graph=True)
+    staged = [out.clone() for (_, _, _, _, out) in items]
+    try:
+        ms_pers = timed(persistent=True)
+        same = all(torch.equal(a, out) for a, (_, _, _, _, out) in zip(staged, items))
+        pers_note = None
+    except st.STError as e:
+        ms_pers, same, pers_note = None, None, str(e)
+    del staged
+    ms = ms_pers if ms_pers is not None else ms_graph
     # the same requests one plan call after another, for comparison
     e0.record()
     for p, _, spec, g, out in items:
@@ -561,9 +575,15 @@ def mixed_batch(args, dev):
     torch.cuda.empty_cache()
     return {"requests": len(reqs), "fields": fields, "ms_per_batch": ms,
             "field_transforms_per_s": fields / (ms * 1e-3),
+            "ms_per_batch_persistent": ms_pers, "ms_per_batch_staged_graph": ms_graph,
+            "persistent_equals_staged_bitwise": same, "persistent_unavailable": pers_note,
+            "kernel_launches_per_run": {"persistent": 1 if ms_pers is not None else None,
+                                        "staged_graph": "one per stage and FFT plan group"},
             "ms_one_call_per_request": ms_seq,
             "mix": "T uniform over {79,159,255,319,511,639}, regular or octahedral, 1-256 fields, seed 1003",
-            "precision": "bf16x3", "launch": "one batch: one launch per stage for all requests, CUDA-graph replay"}
+            "precision": "bf16x3",
+            "launch": ("one persistent cooperative launch for the whole batch (stages separated by grid barriers)"
+                       if ms_pers is not None else "one launch per stage for all requests, CUDA-graph replay")}
 
 
 def serving(args, dev):

@@ -285,8 +285,18 @@ typedef struct {
 } st_batch_item;
 
 st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n);
-/* use_graph != 0: the first run records the launches into a CUDA graph on
- * `stream` and every run replays it (the stream must not be capturing). */
+/* use_graph 0: one launch per stage.  1: the first run records those
+ * launches into a CUDA graph on `stream` and every run replays it (the
+ * stream must not be capturing).  2: the whole batch as one persistent
+ * cooperative launch, one CTA per SM looping over every request's work of
+ * each stage in turn, with bounded grid-wide barriers between the stages (a
+ * barrier that gives up sets bit 16 in the error word of the first item's
+ * plan, reported by st_plan_sync as ST_ERR_TIMEOUT).  Mode 2 takes batches
+ * of one tensor-core precision (BF16x3 or 3xTF32), at most 64 items a
+ * direction, whose rows all have compile-time FFT plans of length up to 4096
+ * (truncations up to T639 on octahedral grids); any other batch returns
+ * ST_ERR_UNSUPPORTED with the reason in st_last_error.  All modes give the
+ * same results bit for bit. */
 st_status st_batch_run(st_batch_t batch, void *stream, int use_graph);
 st_status st_batch_destroy(st_batch_t batch);
 

@@ -67,6 +67,15 @@ def up_to_date() -> bool:
         return fh.read().strip() == _fingerprint()
 
 
+# Translation units with relocatable device code: the persistent batch kernel
+# and the row-FFT bodies it calls at its own CTA width (device-linked below).
+RDC_PREFIXES = ("batch_persistent", "fft_wide_")
+
+
+def _is_rdc(src) -> bool:
+    return os.path.basename(src).startswith(RDC_PREFIXES)
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     """Compile csrc/*.cu for sm_103a and link libst.so (skipped when the
     sources, flags and host architecture are unchanged)."""
@@ -77,7 +86,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc()] + ARCH + flags + ["-c", src, "-o", obj]
+        extra = []
+        if _is_rdc(src):
+            extra = ["-rdc=true"]
+            if os.path.basename(src).startswith("fft_wide_"):
+                extra += ["-maxrregcount=128"]   # callees of a 512-thread kernel
+        cmd = [nvcc()] + ARCH + flags + extra + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -90,6 +104,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     srcs = _sources()
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
+    rdc_objs = [o for src, o in zip(srcs, objs) if _is_rdc(src)]
+    if rdc_objs:
+        dlink = os.path.join(BUILD_DIR, "device_link.o")
+        cmd = [nvcc()] + ARCH + ["-Xcompiler", "-fPIC", "-dlink", "-o", dlink] + rdc_objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"device link failed:\n{r.stdout}\n{r.stderr}")
+        objs = objs + [dlink]
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -3,8 +3,10 @@
 #include "st_internal.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <set>
+#include <string>
 
 using namespace st;
 
@@ -16,6 +18,7 @@ struct st_batch {
         std::vector<SimtJob> simt_inv, simt_dir;
         std::vector<long long> simt_inv_blocks, simt_dir_blocks;
         std::vector<FftJob> fft_inv, fft_dir;
+        std::vector<FftJob> fft_inv_w, fft_dir_w;  // the same rows for 512-thread CTAs
         size_t smem_inv = 0, smem_dir = 0;
         int var_inv = 0, var_dir = 0;  // launch variant of the largest job
         long long big_inv = -1, big_dir = -1;
@@ -25,6 +28,9 @@ struct st_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
+    PersState *pers = nullptr;  // the persistent kernel's tables, when the batch qualifies
+    std::string pers_why;       // why it does not
+    int *err = nullptr;
 };
 
 namespace {
@@ -85,6 +91,45 @@ st_status batch_launch(st_batch *b, cudaStream_t s)
     return ST_OK;
 }
 
+// A job the persistent kernel refuses (its rows did not fit a wide CTA).
+FftJob no_wide_job()
+{
+    FftJob J;
+    memset(&J, 0, sizeof(J));
+    J.kind = -1;
+    return J;
+}
+
+// Per-CTA shared-memory budget of the 512-thread row-FFT CTAs of the
+// persistent kernel: twice a 256-thread CTA's, within one SM's 216 KB.
+int wide_kb(const st_plan *p, int dir) { return std::min(216, 2 * p->fft_kb[dir]); }
+
+// Tables of the persistent kernel, when the batch is one tensor-core
+// precision whose rows all have compile-time FFT plans; else the reason.
+void persistent_setup(st_batch *b)
+{
+    if (b->by_prec.size() != 1) {
+        b->pers_why = "it mixes precisions";
+        return;
+    }
+    auto &kv = *b->by_prec.begin();
+    auto &S = kv.second;
+    PersInput in;
+    in.prec = kv.first;
+    in.sm_count = b->sm_count;
+    in.err = b->err;
+    in.pack = S.pack;
+    in.unpack = S.unpack;
+    in.tc_inv = S.tc_inv;
+    in.tc_dir = S.tc_dir;
+    in.fft_inv = S.fft_inv_w;
+    in.fft_dir = S.fft_dir_w;
+    if (pers_prepare(in, &b->pers) != ST_OK) {
+        b->pers = nullptr;
+        b->pers_why = st_last_error();
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -133,6 +178,14 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n)
             size_t smem = 0;
             if ((r = fft_jobs(p, 0, it.nfields, p->fb, it.grid, fj, &smem))) { delete b; return r; }
             S.fft_inv.insert(S.fft_inv.end(), fj.begin(), fj.end());
+            if (p->prec != P_FP64) {
+                std::vector<FftJob> fw;
+                size_t sw = 0;
+                if (fft_jobs(p, 0, it.nfields, p->fb, it.grid, fw, &sw, wide_kb(p, 0)) == ST_OK)
+                    S.fft_inv_w.insert(S.fft_inv_w.end(), fw.begin(), fw.end());
+                else
+                    S.fft_inv_w.push_back(no_wide_job());
+            }
             S.smem_inv = std::max(S.smem_inv, smem);
             const long long ctas = fft_ctas(fj);
             if (ctas > S.big_inv) { S.big_inv = ctas; S.var_inv = p->fft_var[0]; }
@@ -142,6 +195,14 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n)
             size_t smem = 0;
             if ((r = fft_jobs(p, 1, it.nfields, it.grid, p->fbop, fj, &smem))) { delete b; return r; }
             S.fft_dir.insert(S.fft_dir.end(), fj.begin(), fj.end());
+            if (p->prec != P_FP64) {
+                std::vector<FftJob> fw;
+                size_t sw = 0;
+                if (fft_jobs(p, 1, it.nfields, it.grid, p->fbop, fw, &sw, wide_kb(p, 1)) == ST_OK)
+                    S.fft_dir_w.insert(S.fft_dir_w.end(), fw.begin(), fw.end());
+                else
+                    S.fft_dir_w.push_back(no_wide_job());
+            }
             S.smem_dir = std::max(S.smem_dir, smem);
             const long long ctas = fft_ctas(fj);
             if (ctas > S.big_dir) { S.big_dir = ctas; S.var_dir = p->fft_var[1]; }
@@ -161,6 +222,8 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n)
             S.unpack.push_back(uj);
         }
     }
+    b->err = items[0].plan->err;
+    persistent_setup(b);
     *out = b;
     return ST_OK;
 }
@@ -169,6 +232,13 @@ st_status st_batch_run(st_batch_t b, void *stream, int use_graph)
 {
     if (!b) return ST_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (use_graph == 2) {
+        if (!b->pers) {
+            set_last_error("this batch does not run as one persistent launch: " + b->pers_why);
+            return ST_ERR_UNSUPPORTED;
+        }
+        return pers_launch(b->pers, s);
+    }
     if (!use_graph) return batch_launch(b, s);
     if (!b->exec) {
         // record on a private stream (the legacy default stream cannot be
@@ -197,6 +267,7 @@ st_status st_batch_run(st_batch_t b, void *stream, int use_graph)
 st_status st_batch_destroy(st_batch_t b)
 {
     if (!b) return ST_OK;
+    pers_free(b->pers);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);

@@ -41,7 +41,7 @@ static int fft_fields_for_slot(const st_plan *p, int dir, int nfields, int slot)
 //    padded length in the run.
 // *smem is the most any generic job needs (fast jobs carry their own).
 st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst, std::vector<FftJob> &jobs,
-                   size_t *smem)
+                   size_t *smem, int kb)
 {
     const size_t cs = p->prec == P_FP64 ? 16 : 8;
     const int J = p->J;
@@ -65,7 +65,7 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
     base.err = p->err;
 
     // fast rows
-    const size_t budget = (size_t)p->fft_kb[dir] * 1024;
+    const size_t budget = (size_t)(kb > 0 ? kb : p->fft_kb[dir]) * 1024;
     for (int r = 0; r < p->nfast;) {
         const RowPair &rp = p->rowpairs_h[p->row_order[r]];
         const int id = rp.fast;

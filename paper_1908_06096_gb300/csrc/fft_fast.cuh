@@ -30,14 +30,22 @@
 #include <utility>
 
 namespace st {
-namespace ff {
+// FF_NS: the namespace of this instantiation (the persistent batch kernel
+// compiles the same bodies at its own CTA width in a namespace of its own).
+#ifndef FF_NS
+#define FF_NS ff
+#endif
+#ifndef FF_NT
+#define FF_NT 256
+#endif
+namespace FF_NS {
 
 typedef float2 C;
 
 #ifndef FF_MINB
 #error "define FF_MINB (CTAs per SM the register budget is sized for)"
 #endif
-constexpr int NT = 256;        // threads per CTA
+constexpr int NT = FF_NT;      // threads per CTA
 constexpr int MINB = FF_MINB;  // CTAs per SM the register budget is sized for
 
 __device__ __forceinline__ C cadd(C a, C b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -624,6 +632,9 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
         cp_async_wait_all();
         bar_wait(bar, 0, &abort_raw);
         __syncthreads();
+        // every thread has seen the phase complete: the barrier may be
+        // retired (a persistent CTA sets it up again for its next row)
+        if (threadIdx.x == 0 && !abort_raw) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
         if (abort_raw) {
             // give the copies in flight a bounded chance to land before the
             // shared memory is released
@@ -862,5 +873,5 @@ __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0
         });
 }
 
-}  // namespace ff
+}  // namespace FF_NS
 }  // namespace st

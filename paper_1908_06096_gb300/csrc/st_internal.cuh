@@ -401,7 +401,7 @@ const char *kernel_name(const st_plan *p, int kind);
 
 // ---- job builders and batched launchers ----
 st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst, std::vector<FftJob> &jobs,
-                   size_t *smem);
+                   size_t *smem, int kb = 0);
 st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s,
                           int variant = 0);
 // fast-kernel launch of n jobs of one group (all jobs' kind == group), one direction
@@ -435,6 +435,23 @@ struct TcJob {
 st_status tc_job(st_plan *p, int set, int nfields, void *data, void *out, TcJob *job, int cp = 0);
 st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaStream_t s, int withhold = 0,
                          unsigned long long wait_ns = 2000000000ull);
+
+// ---- persistent batch kernel (batch_persistent.cu) ----
+// The stage jobs of one precision group of a batch; fft jobs built for
+// 512-thread CTAs (fft_jobs with kb = twice the plan's per-CTA budget).
+struct PersInput {
+    int prec = 0;
+    int sm_count = 0;
+    int *err = nullptr;  // error word the grid barriers report into
+    std::vector<PackJob> pack, unpack;
+    std::vector<TcJob> tc_inv, tc_dir;
+    std::vector<FftJob> fft_inv, fft_dir;
+};
+struct PersState;
+st_status pers_prepare(const PersInput &in, PersState **out);
+st_status pers_launch(PersState *ps, cudaStream_t s);
+void pers_free(PersState *ps);
+size_t tc_smem_bytes(int prec, int max_nt, int *stages_out);
 
 // ---- plan helpers (api.cu) ----
 st_status count_launch(st_plan *p, int kind, cudaStream_t s, const std::function<st_status()> &f);

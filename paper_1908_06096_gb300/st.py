@@ -384,8 +384,11 @@ class Batch:
         _check(lib.st_batch_create(ctypes.byref(h), arr, len(items)), "st_batch_create")
         self._h = h
 
-    def run(self, stream=None, graph: bool = True):
-        _check(load().st_batch_run(self._h, _stream_handle(stream), 1 if graph else 0), "st_batch_run")
+    def run(self, stream=None, graph: bool = True, persistent: bool = False):
+        """persistent: the whole batch in one cooperative launch (use_graph 2);
+        raises STError (ST_ERR_UNSUPPORTED) for a batch that does not qualify."""
+        mode = 2 if persistent else (1 if graph else 0)
+        _check(load().st_batch_run(self._h, _stream_handle(stream), mode), "st_batch_run")
 
     def close(self):
         if getattr(self, "_h", None):

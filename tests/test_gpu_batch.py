@@ -170,3 +170,67 @@ def test_batch_rejects_duplicate_plan(st_mod):
     with pytest.raises(st_mod.STError):
         st_mod.Batch([(p, "inv", spec, g, None), (p, "inv", spec, g, None)])
     p.close()
+
+
+PERSIST = [
+    # T, grid, nfields, direction
+    (79, "regular", 7, "round"),
+    (159, "octahedral", 33, "round"),
+    (255, "regular", 3, "inv"),
+    (127, "octahedral", 12, "dir"),
+    (639, "octahedral", 40, "round"),
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_persistent_launch_matches_staged_launches(st_mod, oracle_mod, prec):
+    """The whole batch in one persistent launch gives the per-stage launches'
+    results bit for bit (every field takes the same arithmetic whatever the
+    CTA shape), on two runs in a row; sampled fields against the oracle."""
+    reqs = PERSIST if prec == "bf16x3" else PERSIST[:3]
+    made = [_make(st_mod, 40 + i, T, grid, prec, nf, d) for i, (T, grid, nf, d) in enumerate(reqs)]
+    items = [(p, d, spec if d != "dir" else None, g, out if d != "inv" else None)
+             for (p, spec, g, out), (_, _, _, d) in zip(made, reqs)]
+    b = st_mod.Batch(items)
+    b.run(graph=False)
+    torch.cuda.synchronize()
+    ref = [(g.clone(), out.clone()) for (_, _, g, out) in made]
+    for _ in range(2):
+        for (p, spec, g, out), (_, _, _, d) in zip(made, reqs):
+            out.zero_()
+            if d != "dir":
+                g.zero_()
+        b.run(persistent=True)
+        torch.cuda.synchronize()
+        for (p, spec, g, out), (gr, outr), (_, _, _, d) in zip(made, ref, reqs):
+            p.sync()
+            if d != "dir":
+                assert torch.equal(g, gr)
+            if d != "inv":
+                assert torch.equal(out, outr)
+    # the staged results themselves, one field of each request, vs the oracle
+    for (p, spec, g, out), (T, grid, nf, d) in zip(made, reqs):
+        o = _Oracle(oracle_mod, p)
+        a = spec.double().cpu().numpy()
+        if d != "dir":
+            ref_g = oracle_mod.inv_trans(T, o.rows, o.mu, a[:1])
+            assert per_field_max_rel(g[:1].double().cpu().numpy(), ref_g) < _tol(prec)
+        if d != "inv":
+            ref_s = oracle_mod.dir_trans(T, o.rows, o.mu, o.w, g[:1].double().cpu().numpy())
+            got = out[:1].double().cpu().numpy()
+            assert per_field_max_rel(got[..., 0] + 1j * got[..., 1], ref_s) < _tol(prec)
+    b.close()
+    for p, *_ in made:
+        p.close()
+
+
+def test_persistent_launch_refuses_mixed_precisions(st_mod):
+    made = [_make(st_mod, 60, 31, "regular", "bf16x3", 2, "round"), _make(st_mod, 61, 31, "regular", "fp64", 2, "round")]
+    b = st_mod.Batch([(p, "round", spec, g, out) for (p, spec, g, out) in made])
+    with pytest.raises(st_mod.STError):
+        b.run(persistent=True)
+    b.run(graph=False)
+    torch.cuda.synchronize()
+    b.close()
+    for p, *_ in made:
+        p.close()
