@@ -69,7 +69,7 @@ def up_to_date() -> bool:
 
 # Translation units with relocatable device code: the persistent batch kernel
 # and the row-FFT bodies it calls at its own CTA width (device-linked below).
-RDC_PREFIXES = ("batch_persistent", "fft_wide_")
+RDC_PREFIXES = ("batch_persistent", "fft_half_")
 
 
 def _is_rdc(src) -> bool:
@@ -89,7 +89,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         extra = []
         if _is_rdc(src):
             extra = ["-rdc=true"]
-            if os.path.basename(src).startswith("fft_wide_"):
+            if os.path.basename(src).startswith("fft_half_"):
                 extra += ["-maxrregcount=128"]   # callees of a 512-thread kernel
         cmd = [nvcc()] + ARCH + flags + extra + ["-c", src, "-o", obj]
         if verbose:

@@ -25,7 +25,7 @@ st_status cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA;
 }
 
-size_t tc_smem_bytes(int prec, int max_nt, int *stages_out);
+
 
 static int row_trunc(int T, int n) { return std::min(T, (n - 1) / 2); }
 

@@ -18,7 +18,7 @@ struct st_batch {
         std::vector<SimtJob> simt_inv, simt_dir;
         std::vector<long long> simt_inv_blocks, simt_dir_blocks;
         std::vector<FftJob> fft_inv, fft_dir;
-        std::vector<FftJob> fft_inv_w, fft_dir_w;  // the same rows for 512-thread CTAs
+        std::vector<FftJob> fft_inv_w, fft_dir_w;  // the same rows within a half CTA's shared memory
         size_t smem_inv = 0, smem_dir = 0;
         int var_inv = 0, var_dir = 0;  // launch variant of the largest job
         long long big_inv = -1, big_dir = -1;
@@ -100,9 +100,9 @@ FftJob no_wide_job()
     return J;
 }
 
-// Per-CTA shared-memory budget of the 512-thread row-FFT CTAs of the
-// persistent kernel: twice a 256-thread CTA's, within one SM's 216 KB.
-int wide_kb(const st_plan *p, int dir) { return std::min(216, 2 * p->fft_kb[dir]); }
+// Per-CTA shared-memory budget of the row-FFT jobs of the persistent kernel:
+// each half of its CTA holds one job's CTA, within FF_HALF_BYTES.
+int wide_kb(const st_plan *p, int dir) { return std::min(FF_HALF_BYTES / 1024 - 4, p->fft_kb[dir]); }
 
 // Tables of the persistent kernel, when the batch is one tensor-core
 // precision whose rows all have compile-time FFT plans; else the reason.

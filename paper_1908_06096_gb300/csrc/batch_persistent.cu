@@ -5,10 +5,13 @@
 // every stage of every request of a batch runs in one kernel of one CTA per
 // SM (512 threads): the spectral pack, the tcgen05 Legendre GEMMs of the
 // inverse, the inverse row FFTs, the direct row FFTs, the direct GEMMs and
-// the unpack, each stage a loop of the CTAs over that stage's work items of
-// all requests, separated by grid-wide barriers.  The stage bodies are the
-// per-stage kernels' own (pack_dev.cuh, legendre_tc_dev.cuh, and the row-FFT
-// bodies compiled at this CTA width in fft_wide_*.cu).  Every barrier wait is
+// the unpack, separated by grid-wide barriers.  In the pack, FFT and unpack
+// stages each half of a CTA works as one 256-thread CTA of the per-stage
+// kernels would, claiming the stage's work items of all requests one at a
+// time (the row FFTs longest first); the GEMM stages run the persistent
+// tcgen05 body on six warps.  The stage bodies are the per-stage kernels'
+// own (pack_dev.cuh, legendre_tc_dev.cuh, and the row-FFT bodies compiled
+// for half CTAs in fft_half_*.cu).  Every barrier wait is
 // bounded: past two seconds the CTA records bit 16 in the error word of the
 // batch's first plan and every CTA leaves at its next barrier.
 //
@@ -24,12 +27,12 @@
 
 namespace st {
 
-namespace ffw {
-__device__ void wide_dir_g0(const FftJob &J, const RowPair &rp, int f0);
-__device__ void wide_dir_g1(const FftJob &J, const RowPair &rp, int f0);
-__device__ void wide_inv_g0(const FftJob &J, const RowPair &rp, int f0);
-__device__ void wide_inv_g1(const FftJob &J, const RowPair &rp, int f0);
-}  // namespace ffw
+namespace ffh {
+__device__ void half_dir_g0(const FftJob &J, const RowPair &rp, int f0);
+__device__ void half_dir_g1(const FftJob &J, const RowPair &rp, int f0);
+__device__ void half_inv_g0(const FftJob &J, const RowPair &rp, int f0);
+__device__ void half_inv_g1(const FftJob &J, const RowPair &rp, int f0);
+}  // namespace ffh
 
 namespace pers {
 
@@ -37,17 +40,35 @@ constexpr int THREADS = 512;
 constexpr int ERR_GRID = 16;
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
+// Work-item counters of the stages whose items are claimed one at a time.
+enum { C_PACK = 0, C_FFT_INV = 1, C_FFT_DIR = 2, C_UNPACK = 3, NCLAIM = 4 };
+
+// Units a half claims at once in the pack and FFT stages.
+constexpr int PACK_CHUNK = 4, FFT_CHUNK = 8;
+
+// A GEMM batch as the tcgen05 body reads it: tile prefix and launch facts in
+// kernel parameters, the jobs themselves in global memory.
+struct TcView {
+    const tc::TcLite *job;  // set in the kernel: the CTA's copy in shared memory
+    long long prefix[MAX_JOBS + 1];
+    int njobs, max_nt, stages, withhold_loads;
+    unsigned long long wait_ns;
+};
+
 struct Args {
-    const void *tc_inv, *tc_dir;  // tc::TcBatch<MAX_JOBS> in global memory
+    CUtensorMap maps_inv[MAX_JOBS], maps_dir[MAX_JOBS];  // the GEMM jobs' operand maps (kernel parameters)
+    TcView tc_inv, tc_dir;
+    const tc::TcLite *tcj_inv, *tcj_dir;  // the GEMM jobs in global memory
     const PackJob *pack, *unpack;
     const long long *pack_pre, *unpack_pre;
     const FftJob *fi, *fd;
     const long long *fi_pre, *fd_pre;
     int npack, nunpack, nfi, nfd;
     long long ntc_inv, ntc_dir;   // GEMM tiles of each direction
-    unsigned long long *count;    // grid-barrier arrivals (zeroed before each launch)
+    unsigned long long *count;    // grid-barrier arrivals, then NCLAIM claim counters (zeroed before each launch)
     int *err;
 };
+static_assert(sizeof(Args) <= 32000, "kernel parameters");
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
 {
@@ -87,57 +108,137 @@ __device__ bool grid_sync(const Args &A, unsigned long long target, volatile int
 
 __device__ __forceinline__ void half_sync(int h) { asm volatile("bar.sync %0, 256;" ::"r"(2 + h) : "memory"); }
 
-// One stage of pack (UNPACK false) or unpack blocks: each CTA runs two
-// 256-thread blocks at a time, one per half, each with its own tile and
-// barrier.
+// The next work item of a stage for this half (thread 0 of the half claims
+// it, the half reads it after its barrier).
+__device__ __forceinline__ long long claim(unsigned long long *ctr, long long *slot, int h, int chunk)
+{
+    if ((threadIdx.x & 255) == 0) *slot = (long long)atomicAdd(ctr, (unsigned long long)chunk);
+    half_sync(h);
+    const long long u = *(volatile long long *)slot;
+    half_sync(h);
+    return u;
+}
+
+// One stage of pack (UNPACK false) or unpack blocks: the CTA runs eight
+// 64-thread blocks at a time, each with its own tile and barrier, claiming
+// PACK_CHUNK blocks at once; the stage's job table is first copied to shared
+// memory.
 template <bool UNPACK, int S>
-__device__ void pack_stage(const PackJob *jobs, const long long *pre, int n, unsigned char *smem)
+__device__ void pack_stage(const Args &A, const PackJob *jobs_g, const long long *pre_g, int n,
+                           unsigned char *smem, long long *slots)
 {
     if (n <= 0) return;
-    const int h = threadIdx.x >> 8, w = (threadIdx.x >> 5) & 7, lane = threadIdx.x & 31;
-    float(*tile)[65] = (float(*)[65])(smem + h * (32 * 65 * sizeof(float)));
+    constexpr int NB = 8, NWB = THREADS / 32 / NB;  // blocks per CTA, warps per block
+    constexpr size_t TILE = 32 * 65 * sizeof(float);
+    PackJob *jobs = (PackJob *)(smem + NB * TILE);
+    long long *pre = (long long *)(jobs + MAX_JOBS);
+    for (int i = threadIdx.x; i < n * (int)(sizeof(PackJob) / 8); i += THREADS)
+        ((long long *)jobs)[i] = ((const long long *)jobs_g)[i];
+    for (int i = threadIdx.x; i <= n; i += THREADS) pre[i] = pre_g[i];
+    __syncthreads();
+    const int blk = threadIdx.x / (32 * NWB), w = (threadIdx.x >> 5) % NWB, lane = threadIdx.x & 31;
+    float(*tile)[65] = (float(*)[65])(smem + blk * TILE);
+    auto bsync = [blk] { asm volatile("bar.sync %0, %1;" ::"r"(2 + blk), "n"(32 * NWB) : "memory"); };
     const long long tot = pre[n];
-    for (long long u = 2LL * blockIdx.x + h; u < tot; u += 2LL * gridDim.x) {
-        const int q = find_job<1>(pre, n, u);
-        const int b = (int)(u - pre[q]);
-        if (UNPACK) unpack_block<float>(jobs[q], b, tile, w, lane, [h] { half_sync(h); });
-        else pack_block<float, S>(jobs[q], b, tile, w, lane, [h] { half_sync(h); });
+    unsigned long long *ctr = A.count + 1 + (UNPACK ? C_UNPACK : C_PACK);
+    for (;;) {
+        if ((threadIdx.x & (32 * NWB - 1)) == 0) slots[blk] = (long long)atomicAdd(ctr, (unsigned long long)PACK_CHUNK);
+        bsync();
+        const long long u0 = *(volatile long long *)&slots[blk];
+        bsync();
+        if (u0 >= tot) break;
+        for (long long u = u0; u < u0 + PACK_CHUNK && u < tot; ++u) {
+            const int q = find_job<1>(pre, n, u);
+            const int b = (int)(u - pre[q]);
+            if (UNPACK) unpack_block<float, 1, NWB>(jobs[q], b, tile, w, lane, bsync);
+            else pack_block<float, S, 1, NWB>(jobs[q], b, tile, w, lane, bsync);
+        }
     }
 }
 
-// One stage of row FFTs: the CTAs take the stage's (row pair, field group)
-// items in turn.
-// A row whose bounded wait gave up (error bit 8 of its plan) ends the
-// stage for this CTA and marks the batch abandoned.
+// One stage of row FFTs: each half takes (row pair, field group) items in
+// turn, FFT_CHUNK a claim, the stage's jobs sorted longest rows first; the
+// next item's row description is fetched asynchronously while the current
+// item runs.  A row whose bounded wait gave up (error bit 8 of its plan)
+// ends the stage for this half and marks the batch abandoned.
 template <int DIR>
-__device__ void fft_stage(const Args &A, const FftJob *jobs, const long long *pre, int n, RowPair *rp,
-                          volatile int *stop)
+__device__ void fft_stage(const Args &A, const FftJob *jobs, const long long *pre, int n, RowPair (*rps)[2],
+                          long long *slots)
 {
     if (n <= 0) return;
+    const int h = threadIdx.x >> 8, t = threadIdx.x & 255;
+    constexpr int NW = (int)(sizeof(RowPair) / sizeof(int));
     const long long tot = pre[n];
-    for (long long u = blockIdx.x; u < tot; u += gridDim.x) {
-        const int q = find_job<1>(pre, n, u);
+    unsigned long long *ctr = A.count + 1 + (DIR ? C_FFT_DIR : C_FFT_INV);
+    // item u of job q: its row-pair entry
+    auto fetch = [&](int q, long long u, RowPair *dst) {
         const FftJob &J = jobs[q];
-        const int b = (int)(u - pre[q]);
-        const int rr = b / J.nfg;
-        const int f0 = (b - rr * J.nfg) * J.G;
-        const int nw = (int)(sizeof(RowPair) / sizeof(int));
+        const int rr = (int)(u - pre[q]) / J.nfg;
         const int *src = (const int *)(J.rps + J.r0 + rr);
-        for (int i = threadIdx.x; i < nw; i += THREADS) ((int *)rp)[i] = src[i];
-        __syncthreads();
-        if (J.kind == 0) {
-            if (DIR) ffw::wide_dir_g0(J, *rp, f0);
-            else ffw::wide_inv_g0(J, *rp, f0);
-        } else {
-            if (DIR) ffw::wide_dir_g1(J, *rp, f0);
-            else ffw::wide_inv_g1(J, *rp, f0);
+        if (t < NW)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared((int *)dst + t)),
+                         "l"(src + t)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int *errp = jobs[0].err;
+    for (;;) {
+        // claim the next FFT_CHUNK items, or stop (the claimed batch is done,
+        // or the last item's plan recorded a bounded wait that gave up)
+        if (t == 0) {
+            const bool failed = (*(volatile const int *)errp & 8) != 0;
+            if (failed) atomicOr(A.err, ERR_GRID);
+            slots[h] = failed ? tot : (long long)atomicAdd(ctr, (unsigned long long)FFT_CHUNK);
         }
-        if (threadIdx.x == 0) {
-            *stop = (*(volatile int *)J.err & 8) != 0;
-            if (*stop) atomicOr(A.err, ERR_GRID);
+        half_sync(h);
+        const long long u0 = *(volatile long long *)&slots[h];
+        half_sync(h);
+        if (u0 >= tot) break;
+        const long long u1 = u0 + FFT_CHUNK < tot ? u0 + FFT_CHUNK : tot;
+        int q = find_job<1>(pre, n, u0);
+        fetch(q, u0, &rps[h][0]);
+        int qn = q;
+        for (long long u = u0; u < u1; ++u) {
+            const int buf = (int)((u - u0) & 1);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            half_sync(h);
+            if (u + 1 < u1) {
+                while (pre[qn + 1] <= u + 1) ++qn;
+                fetch(qn, u + 1, &rps[h][buf ^ 1]);
+            }
+            const FftJob &J = jobs[q];
+            const int b = (int)(u - pre[q]);
+            const int f0 = (b - (b / J.nfg) * J.nfg) * J.G;
+            if (J.kind == 0) {
+                if (DIR) ffh::half_dir_g0(J, rps[h][buf], f0);
+                else ffh::half_inv_g0(J, rps[h][buf], f0);
+            } else {
+                if (DIR) ffh::half_dir_g1(J, rps[h][buf], f0);
+                else ffh::half_inv_g1(J, rps[h][buf], f0);
+            }
+            q = qn;
+            half_sync(h);
         }
-        __syncthreads();
-        if (*stop) return;
+        errp = jobs[q].err;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// One GEMM stage: the jobs are copied to shared memory (their per-tile
+// lookups then cost no global round trips), then six warps run the tcgen05
+// body over the stage's tiles.
+template <int KIND>
+__device__ void gemm_stage(const TcView &V, const tc::TcLite *jobs_g, const CUtensorMap *maps, long long tiles,
+                           tc::TcLite *jobs_s, unsigned char *smem)
+{
+    if (tiles <= 0) return;
+    for (int i = threadIdx.x; i < V.njobs * (int)(sizeof(tc::TcLite) / 8); i += THREADS)
+        ((long long *)jobs_s)[i] = ((const long long *)jobs_g)[i];
+    __syncthreads();
+    if (threadIdx.x < tc::THREADS) {
+        TcView v = V;
+        v.job = jobs_s;
+        tc::leg_tc_body<KIND>(v, smem, blockIdx.x, gridDim.x, false, maps);
     }
 }
 
@@ -145,24 +246,24 @@ template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1) k_batch_persistent(const __grid_constant__ Args A)
 {
     extern __shared__ __align__(1024) unsigned char pers_smem[];
-    __shared__ RowPair rp;
+    __shared__ RowPair rps[2][2];
+    __shared__ long long slots[8];
     __shared__ int abort_s;
+    __shared__ __align__(16) tc::TcLite tcj[MAX_JOBS];
     constexpr int S = KIND == 0 ? S_BF16_SPLIT : S_TF32_SPLIT;
     const unsigned long long g = gridDim.x;
 
-    pack_stage<false, S>(A.pack, A.pack_pre, A.npack, pers_smem);
+    pack_stage<false, S>(A, A.pack, A.pack_pre, A.npack, pers_smem, slots);
     if (!grid_sync(A, 1 * g, &abort_s)) return;
-    if (A.ntc_inv > 0 && threadIdx.x < tc::THREADS)
-        tc::leg_tc_body<KIND>(*(const tc::TcBatch<MAX_JOBS> *)A.tc_inv, pers_smem, blockIdx.x, gridDim.x, false);
+    gemm_stage<KIND>(A.tc_inv, A.tcj_inv, A.maps_inv, A.ntc_inv, tcj, pers_smem);
     if (!grid_sync(A, 2 * g, &abort_s)) return;
-    fft_stage<0>(A, A.fi, A.fi_pre, A.nfi, &rp, &abort_s);
+    fft_stage<0>(A, A.fi, A.fi_pre, A.nfi, rps, slots);
     if (!grid_sync(A, 3 * g, &abort_s)) return;
-    fft_stage<1>(A, A.fd, A.fd_pre, A.nfd, &rp, &abort_s);
+    fft_stage<1>(A, A.fd, A.fd_pre, A.nfd, rps, slots);
     if (!grid_sync(A, 4 * g, &abort_s)) return;
-    if (A.ntc_dir > 0 && threadIdx.x < tc::THREADS)
-        tc::leg_tc_body<KIND>(*(const tc::TcBatch<MAX_JOBS> *)A.tc_dir, pers_smem, blockIdx.x, gridDim.x, false);
+    gemm_stage<KIND>(A.tc_dir, A.tcj_dir, A.maps_dir, A.ntc_dir, tcj, pers_smem);
     if (!grid_sync(A, 5 * g, &abort_s)) return;
-    pack_stage<true, S>(A.unpack, A.unpack_pre, A.nunpack, pers_smem);
+    pack_stage<true, S>(A, A.unpack, A.unpack_pre, A.nunpack, pers_smem, slots);
 }
 
 }  // namespace pers
@@ -192,7 +293,7 @@ long long prefix_of(const std::vector<J> &jobs, std::vector<long long> &pre, lon
 long long pack_units(const PackJob &J) { return (long long)J.nm * J.nft; }
 long long fft_units(const FftJob &J) { return (long long)J.J * J.nfg; }
 
-st_status tc_batch(int prec, const std::vector<TcJob> &jobs, tc::TcBatch<MAX_JOBS> *B, size_t *smem, long long *tiles)
+st_status tc_view(int prec, const std::vector<TcJob> &jobs, pers::TcView *B, size_t *smem, long long *tiles)
 {
     memset((void *)B, 0, sizeof(*B));
     B->njobs = (int)jobs.size();
@@ -202,14 +303,13 @@ st_status tc_batch(int prec, const std::vector<TcJob> &jobs, tc::TcBatch<MAX_JOB
     int max_nt = 16;
     for (size_t q = 0; q < jobs.size(); ++q) {
         B->prefix[q] = tot;
-        B->job[q] = jobs[q];
         tot += jobs[q].ntiles;
         max_nt = std::max(max_nt, jobs[q].max_nt);
     }
     B->prefix[jobs.size()] = tot;
     B->max_nt = max_nt;
     int S = 0;
-    *smem = tc_smem_bytes(prec, max_nt, &S);
+    *smem = tc_smem_bytes(prec, max_nt, &S, 2 * (size_t)FF_HALF_BYTES);
     if (S < 2) return ST_ERR_UNSUPPORTED;
     B->stages = S;
     *tiles = tot;
@@ -229,71 +329,80 @@ st_status pers_prepare(const PersInput &in, PersState **out)
         set_last_error("the persistent batch kernel takes at most 64 items a direction");
         return ST_ERR_UNSUPPORTED;
     }
-    size_t fft_smem = 0;
     for (const auto *v : {&in.fft_inv, &in.fft_dir})
         for (const FftJob &J : *v) {
             if (J.kind != 0 && J.kind != 1) {
                 set_last_error("a row of this batch has no compile-time FFT plan of lengths up to 4096");
                 return ST_ERR_UNSUPPORTED;
             }
-            fft_smem = std::max(fft_smem, (size_t)J.smem);
+            if (J.smem > FF_HALF_BYTES) {
+                set_last_error("a row job of this batch needs more shared memory than half a CTA holds");
+                return ST_ERR_UNSUPPORTED;
+            }
         }
-    auto *B0 = new tc::TcBatch<MAX_JOBS>;
-    auto *B1 = new tc::TcBatch<MAX_JOBS>;
+    // row-FFT jobs longest rows first, so that the items claimed last are short
+    auto by_size = [](const FftJob &a, const FftJob &b) {
+        return (long long)a.G * a.Sslot > (long long)b.G * b.Sslot;
+    };
+    std::vector<FftJob> fi = in.fft_inv, fd = in.fft_dir;
+    std::stable_sort(fi.begin(), fi.end(), by_size);
+    std::stable_sort(fd.begin(), fd.end(), by_size);
+    auto *ps = new PersState;
+    ps->prec = in.prec;
+    pers::Args &A = ps->args;
     size_t sm0 = 0, sm1 = 0;
     long long t0 = 0, t1 = 0;
-    st_status r = tc_batch(in.prec, in.tc_inv, B0, &sm0, &t0);
-    if (r == ST_OK) r = tc_batch(in.prec, in.tc_dir, B1, &sm1, &t1);
+    st_status r = tc_view(in.prec, in.tc_inv, &A.tc_inv, &sm0, &t0);
+    if (r == ST_OK) r = tc_view(in.prec, in.tc_dir, &A.tc_dir, &sm1, &t1);
     if (r != ST_OK) {
-        delete B0;
-        delete B1;
+        delete ps;
         set_last_error("no GEMM pipeline fits the persistent batch kernel's shared memory");
         return r;
     }
     std::vector<long long> pp, up, fip, fdp;
     prefix_of<PackJob>(in.pack, pp, pack_units);
     prefix_of<PackJob>(in.unpack, up, pack_units);
-    prefix_of<FftJob>(in.fft_inv, fip, fft_units);
-    prefix_of<FftJob>(in.fft_dir, fdp, fft_units);
+    prefix_of<FftJob>(fi, fip, fft_units);
+    prefix_of<FftJob>(fd, fdp, fft_units);
 
     // one CTA per SM: ask for more shared memory than two CTAs could share
-    size_t smem = std::max({sm0, sm1, fft_smem, (size_t)2 * 32 * 65 * sizeof(float), (size_t)120 * 1024});
+    size_t smem = std::max({sm0, sm1, (size_t)2 * FF_HALF_BYTES, (size_t)8 * 32 * 65 * sizeof(float) + 8192});
     if (smem > 227 * 1024) {
-        delete B0;
-        delete B1;
+        delete ps;
         set_last_error("the persistent batch kernel needs more shared memory than a CTA has");
         return ST_ERR_UNSUPPORTED;
     }
 
     // device tables, one allocation
     size_t off = 0;
-    const size_t o_tc0 = off; off = up256(off + sizeof(*B0));
-    const size_t o_tc1 = off; off = up256(off + sizeof(*B1));
+    const size_t o_ti = off; off = up256(off + sizeof(tc::TcLite) * in.tc_inv.size());
+    const size_t o_td = off; off = up256(off + sizeof(tc::TcLite) * in.tc_dir.size());
     const size_t o_pk = off; off = up256(off + sizeof(PackJob) * in.pack.size());
     const size_t o_pkp = off; off = up256(off + sizeof(long long) * pp.size());
     const size_t o_up = off; off = up256(off + sizeof(PackJob) * in.unpack.size());
     const size_t o_upp = off; off = up256(off + sizeof(long long) * up.size());
-    const size_t o_fi = off; off = up256(off + sizeof(FftJob) * in.fft_inv.size());
+    const size_t o_fi = off; off = up256(off + sizeof(FftJob) * fi.size());
     const size_t o_fip = off; off = up256(off + sizeof(long long) * fip.size());
-    const size_t o_fd = off; off = up256(off + sizeof(FftJob) * in.fft_dir.size());
+    const size_t o_fd = off; off = up256(off + sizeof(FftJob) * fd.size());
     const size_t o_fdp = off; off = up256(off + sizeof(long long) * fdp.size());
-    const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long));
+    const size_t o_cnt = off; off = up256(off + sizeof(unsigned long long) * (1 + pers::NCLAIM));
     std::vector<unsigned char> host(off, 0);
-    memcpy(host.data() + o_tc0, (const void *)B0, sizeof(*B0));
-    memcpy(host.data() + o_tc1, (const void *)B1, sizeof(*B1));
-    delete B0;
-    delete B1;
+    for (int dir = 0; dir < 2; ++dir) {
+        const std::vector<TcJob> &v = dir ? in.tc_dir : in.tc_inv;
+        tc::TcLite *t = (tc::TcLite *)(host.data() + (dir ? o_td : o_ti));
+        for (size_t q = 0; q < v.size(); ++q)
+            t[q] = tc::TcLite{v[q].groups, v[q].tiles, v[q].tab, v[q].out, v[q].err, v[q].ntiles,
+                          v[q].ncm, v[q].C, v[q].Cp, v[q].max_nt};
+    }
     if (!in.pack.empty()) memcpy(host.data() + o_pk, in.pack.data(), sizeof(PackJob) * in.pack.size());
     memcpy(host.data() + o_pkp, pp.data(), sizeof(long long) * pp.size());
     if (!in.unpack.empty()) memcpy(host.data() + o_up, in.unpack.data(), sizeof(PackJob) * in.unpack.size());
     memcpy(host.data() + o_upp, up.data(), sizeof(long long) * up.size());
-    if (!in.fft_inv.empty()) memcpy(host.data() + o_fi, in.fft_inv.data(), sizeof(FftJob) * in.fft_inv.size());
+    if (!fi.empty()) memcpy(host.data() + o_fi, fi.data(), sizeof(FftJob) * fi.size());
     memcpy(host.data() + o_fip, fip.data(), sizeof(long long) * fip.size());
-    if (!in.fft_dir.empty()) memcpy(host.data() + o_fd, in.fft_dir.data(), sizeof(FftJob) * in.fft_dir.size());
+    if (!fd.empty()) memcpy(host.data() + o_fd, fd.data(), sizeof(FftJob) * fd.size());
     memcpy(host.data() + o_fdp, fdp.data(), sizeof(long long) * fdp.size());
 
-    auto *ps = new PersState;
-    ps->prec = in.prec;
     cudaError_t e = cudaMalloc(&ps->dev, off);
     if (e != cudaSuccess) {
         delete ps;
@@ -305,9 +414,10 @@ st_status pers_prepare(const PersInput &in, PersState **out)
         return cuda_fail(e, "cudaMemcpy (persistent batch tables)");
     }
     unsigned char *d = (unsigned char *)ps->dev;
-    pers::Args &A = ps->args;
-    A.tc_inv = d + o_tc0;
-    A.tc_dir = d + o_tc1;
+    A.tcj_inv = (const tc::TcLite *)(d + o_ti);
+    A.tcj_dir = (const tc::TcLite *)(d + o_td);
+    for (size_t q = 0; q < in.tc_inv.size(); ++q) A.maps_inv[q] = in.tc_inv[q].map;
+    for (size_t q = 0; q < in.tc_dir.size(); ++q) A.maps_dir[q] = in.tc_dir[q].map;
     A.pack = (const PackJob *)(d + o_pk);
     A.pack_pre = (const long long *)(d + o_pkp);
     A.unpack = (const PackJob *)(d + o_up);
@@ -318,8 +428,8 @@ st_status pers_prepare(const PersInput &in, PersState **out)
     A.fd_pre = (const long long *)(d + o_fdp);
     A.npack = (int)in.pack.size();
     A.nunpack = (int)in.unpack.size();
-    A.nfi = (int)in.fft_inv.size();
-    A.nfd = (int)in.fft_dir.size();
+    A.nfi = (int)fi.size();
+    A.nfd = (int)fd.size();
     A.ntc_inv = t0;
     A.ntc_dir = t1;
     A.count = (unsigned long long *)(d + o_cnt);
@@ -347,7 +457,7 @@ st_status pers_prepare(const PersInput &in, PersState **out)
 st_status pers_launch(PersState *ps, cudaStream_t s)
 {
     if (!ps) return ST_ERR_ARG;
-    ST_CUDA(cudaMemsetAsync(ps->args.count, 0, sizeof(unsigned long long), s));
+    ST_CUDA(cudaMemsetAsync(ps->args.count, 0, sizeof(unsigned long long) * (1 + pers::NCLAIM), s));
     const void *k =
         ps->prec == P_BF16X3 ? (const void *)pers::k_batch_persistent<0> : (const void *)pers::k_batch_persistent<1>;
     void *params[] = {(void *)&ps->args};

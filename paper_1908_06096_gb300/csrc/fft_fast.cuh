@@ -38,6 +38,23 @@ namespace st {
 #ifndef FF_NT
 #define FF_NT 256
 #endif
+// Whole CTA or half CTA: a translation unit that runs the bodies in one half
+// of a 512-thread CTA (the persistent batch kernel: two row-FFT items per SM
+// at a time, as two 256-thread CTAs would) defines FF_HALVES; each half then
+// has its own thread index, barrier and FF_HALF_BYTES of shared memory.
+#ifdef FF_HALVES
+#define FF_HALF (threadIdx.x >> 8)
+#define FF_TID (threadIdx.x & 255)
+#define FF_SYNC() asm volatile("bar.sync %0, 256;" ::"r"(4 + FF_HALF) : "memory")
+#define FF_SMEM_OFF (FF_HALF * FF_HALF_BYTES)
+#define FF_NHALF 2
+#else
+#define FF_HALF 0
+#define FF_TID threadIdx.x
+#define FF_SYNC() __syncthreads()
+#define FF_SMEM_OFF 0
+#define FF_NHALF 1
+#endif
 namespace FF_NS {
 
 typedef float2 C;
@@ -380,7 +397,7 @@ __device__ __forceinline__ void stage(C *x, int G, const C *__restrict__ tw, con
 {
     constexpr int L = PL::L, R = PL::template R<s>(), NS = PL::template NS<s>();
     constexpr int ST = NS / R, NB = L / R, TWS = L / NS, SL = PL::SL;
-    for (int i = threadIdx.x; i < G * NB; i += NT) {
+    for (int i = FF_TID; i < G * NB; i += NT) {
         const int f = i / NB, u = i - f * NB;
         const int b = u / ST, n1 = u - b * ST;
         C *xf = x + f * SL;
@@ -423,11 +440,11 @@ template <class PL, bool DIT>
 __device__ __forceinline__ void middle_stages(C *x, int G, const C *tw)
 {
     if constexpr (!DIT) {
-        if constexpr (PL::P >= 3) { stage<PL, 2, false>(x, G, tw, nullptr); __syncthreads(); }
-        if constexpr (PL::P >= 4) { stage<PL, 3, false>(x, G, tw, nullptr); __syncthreads(); }
+        if constexpr (PL::P >= 3) { stage<PL, 2, false>(x, G, tw, nullptr); FF_SYNC(); }
+        if constexpr (PL::P >= 4) { stage<PL, 3, false>(x, G, tw, nullptr); FF_SYNC(); }
     } else {
-        if constexpr (PL::P >= 4) { stage<PL, 3, true>(x, G, tw, nullptr); __syncthreads(); }
-        if constexpr (PL::P >= 3) { stage<PL, 2, true>(x, G, tw, nullptr); __syncthreads(); }
+        if constexpr (PL::P >= 4) { stage<PL, 3, true>(x, G, tw, nullptr); FF_SYNC(); }
+        if constexpr (PL::P >= 3) { stage<PL, 2, true>(x, G, tw, nullptr); FF_SYNC(); }
     }
 }
 
@@ -437,7 +454,7 @@ template <class PL, class IN>
 __device__ __forceinline__ void stage1_in(C *x, int G, const C *__restrict__ tw, IN in)
 {
     constexpr int L = PL::L, R = PL::template R<1>(), ST = L / R, SL = PL::SL;
-    for (int i = threadIdx.x; i < G * ST; i += NT) {
+    for (int i = FF_TID; i < G * ST; i += NT) {
         const int f = i / ST, n = i - f * ST;
         C v[R];
 #pragma unroll
@@ -466,7 +483,7 @@ __device__ __forceinline__ void stage1_raw(C *x, int G, const C *__restrict__ tw
 {
     constexpr int L = PL::L, R = PL::template R<1>(), ST = L / R, SL = PL::SL;
     static_assert(ST <= NT, "one stage-1 item per thread per field");
-    const int n = threadIdx.x;
+    const int n = FF_TID;
     for (int f = 0; f < G; ++f) {
         const float *raw = (const float *)(x + raw_at(f, SL));
         C v[R];
@@ -477,7 +494,7 @@ __device__ __forceinline__ void stage1_raw(C *x, int G, const C *__restrict__ tw
                 v[q] = e < N ? cmul(cz[q], make_float2(raw[e], raw[N + e])) : make_float2(0.f, 0.f);
             }
         }
-        __syncthreads();
+        FF_SYNC();
         if (n < ST) {
             dft<R>(v);
             twiddle_pow<R>(v, tw[n]);
@@ -497,7 +514,7 @@ template <class PL, class PRE, class OUT>
 __device__ __forceinline__ void stage1_out(C *x, int G, const C *__restrict__ tw, PRE pre, OUT out)
 {
     constexpr int L = PL::L, R = PL::template R<1>(), ST = L / R, SL = PL::SL;
-    for (int i = threadIdx.x; i < G * ST; i += NT) {
+    for (int i = FF_TID; i < G * ST; i += NT) {
         const int f = i / ST, n = i - f * ST;
         C pv[R];
 #pragma unroll
@@ -568,7 +585,7 @@ template <class PL>
 __device__ __forceinline__ void load_tables(C *tws, const C *twg)
 {
     if constexpr (PL::TW_SMEM)
-        for (int t = threadIdx.x; t < PL::TWN; t += NT) cp_async8(&tws[t], &twg[t]);
+        for (int t = FF_TID; t < PL::TWN; t += NT) cp_async8(&tws[t], &twg[t]);
     cp_async_commit();
 }
 
@@ -580,7 +597,7 @@ template <class PL>
 __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *x = (C *)smem_raw;
+    C *x = (C *)(smem_raw + FF_SMEM_OFF);
     constexpr int L = PL::L, SL = PL::SL;
     const int N = rp.N, M = rp.M;
     // fields of this CTA (the last CTA of a row may hold fewer than J.G)
@@ -606,10 +623,12 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
     const bool raw = kRawFits && G > 0 && ((on | os | (long long)N | npts) & 3) == 0 &&
                      (reinterpret_cast<uintptr_t>(J.src) & 15) == 0 && (smem_addr(x) & 15) == 0;
     if (raw) {
-        __shared__ __align__(8) unsigned long long rbar;
-        __shared__ int abort_raw;
+        __shared__ __align__(8) unsigned long long rbar_[FF_NHALF];
+        __shared__ int abort_[FF_NHALF];
+        unsigned long long &rbar = rbar_[FF_HALF];
+        int &abort_raw = abort_[FF_HALF];
         const uint32_t bar = smem_addr(&rbar);
-        if (threadIdx.x == 0) {
+        if (FF_TID == 0) {
             abort_raw = 0;
             bar_init_expect(bar, (uint32_t)(G * 8 * N));
             for (int f = 0; f < G; ++f) {
@@ -618,27 +637,27 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
                 bulk_copy(d + N, grid + f * npts + os, 4u * N, bar);
             }
         }
-        __syncthreads();
+        FF_SYNC();
         // the chirp factors of this thread's stage-1 elements, loaded while
         // the rows are in flight
         constexpr int R1 = PL::template R<1>(), ST1 = PL::L / R1;
         C cz[R1];
 #pragma unroll
         for (int q = 0; q < R1; ++q) {
-            const int e = threadIdx.x + q * ST1;
+            const int e = FF_TID + q * ST1;
             cz[q] = make_float2(1.f, 0.f);
-            if (blue && threadIdx.x < ST1 && e < N) cz[q] = __ldg(&chirp[e]);
+            if (blue && FF_TID < ST1 && e < N) cz[q] = __ldg(&chirp[e]);
         }
         cp_async_wait_all();
         bar_wait(bar, 0, &abort_raw);
-        __syncthreads();
+        FF_SYNC();
         // every thread has seen the phase complete: the barrier may be
         // retired (a persistent CTA sets it up again for its next row)
-        if (threadIdx.x == 0 && !abort_raw) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+        if (FF_TID == 0 && !abort_raw) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
         if (abort_raw) {
             // give the copies in flight a bounded chance to land before the
             // shared memory is released
-            if (threadIdx.x == 0) {
+            if (FF_TID == 0) {
                 atomicOr(J.err, FF_ERR_WAIT);
                 const unsigned long long t0 = gtime();
                 while (!bar_test(bar, 0) && gtime() - t0 < FF_WAIT_NS) {
@@ -659,12 +678,12 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
         });
     }
     cp_async_wait_all();
-    __syncthreads();
+    FF_SYNC();
     middle_stages<PL, false>(x, G, tw);
     constexpr int P = PL::P;
     if (blue) {
         stage<PL, P, false, true>(x, G, tw, kern);
-        __syncthreads();
+        FF_SYNC();
         middle_stages<PL, true>(x, G, tw);
         // y at natural places; keep 0 .. M and L - M .. L - 1
         stage1_out<PL>(
@@ -675,7 +694,7 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
     } else {
         stage<PL, P, false>(x, G, tw, nullptr);
     }
-    __syncthreads();
+    FF_SYNC();
 
     // Z_m and Z_{-m}; north spectrum (Z_m + conj Z_{-m}) / 2, south
     // -i (Z_m - conj Z_{-m}) / 2; E, O their sum and difference over N.
@@ -689,7 +708,7 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
     const long long Rp = J.Rp, ps = J.ps;
     // four items per thread per round, their chirp loads issued first
     const int nitems = (M + 1) * G2;
-    for (int base = threadIdx.x; base < nitems; base += 4 * NT) {
+    for (int base = FF_TID; base < nitems; base += 4 * NT) {
     C cmu[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -745,7 +764,7 @@ template <class PL>
 __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *x = (C *)smem_raw;
+    C *x = (C *)(smem_raw + FF_SMEM_OFF);
     constexpr int L = PL::L, SL = PL::SL;
     const int N = rp.N, M = rp.M;
     const int G = max(0, min(J.G, J.nfields - f0));
@@ -770,7 +789,7 @@ __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0
     const int mtop = blue ? M : N / 2;
     const int nitems = (mtop + 1) * G2;
     float4 *stg = (float4 *)(tws + (PL::TW_SMEM ? PL::TWN : 0));
-    for (int idx = threadIdx.x; idx < nitems; idx += NT) {
+    for (int idx = FF_TID; idx < nitems; idx += NT) {
         const int m = idx / G2, f = 2 * (idx - m * G2);
         float4 *d = stg + 2 * idx;
         if (m <= M) {
@@ -794,13 +813,13 @@ __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0
     }
     cp_async_commit();
     cp_async_wait_all();
-    __syncthreads();
+    FF_SYNC();
 
     // Bluestein rows keep the inputs at their natural places (0 .. M and
     // L - M .. L - 1, the rest is zero by index in stage 1); mode-0 rows run
     // DIT passes only, so every place 0 .. N - 1 is written, in the
     // digit-reversed order.
-    for (int idx = threadIdx.x; idx < nitems; idx += NT) {
+    for (int idx = FF_TID; idx < nitems; idx += NT) {
         const int m = idx / G2, f = 2 * (idx - m * G2);
         const bool two = f + 1 < G;
         const float4 sv = stg[2 * idx], av = stg[2 * idx + 1];
@@ -834,7 +853,7 @@ __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0
         }
     }
     cp_async_wait_all();
-    __syncthreads();
+    FF_SYNC();
 
     constexpr int P = PL::P;
     if (blue) {
@@ -845,13 +864,13 @@ __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0
         });
         // stage 1 reads and writes only its own butterfly's places, so it can
         // run in place; every place is written (zeros where the input was zero)
-        __syncthreads();
+        FF_SYNC();
         middle_stages<PL, false>(x, G, tw);
         stage<PL, P, false, true>(x, G, tw, kern);
-        __syncthreads();
+        FF_SYNC();
     } else {
         stage<PL, P, true>(x, G, tw, nullptr);
-        __syncthreads();
+        FF_SYNC();
     }
     middle_stages<PL, true>(x, G, tw);
     float *grid = (float *)J.dst + (long long)f0 * J.npts;

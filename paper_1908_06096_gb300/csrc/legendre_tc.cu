@@ -91,12 +91,12 @@ static int tc_max_nt(const st_plan *p, int set)
     return mx;
 }
 
-size_t tc_smem_bytes(int prec, int max_nt, int *stages_out)
+size_t tc_smem_bytes(int prec, int max_nt, int *stages_out, size_t cap)
 {
     const size_t a = 2 * (size_t)TC_M * 128;  // two planes of 128 columns x 128 bytes
     const size_t stage = a + 2 * (size_t)max_nt * 128;
     const size_t ctrl = 256;
-    const size_t limit = 227 * 1024 - 1024 - ctrl;
+    const size_t limit = (cap ? cap : 227 * 1024) - 1024 - ctrl;
     int S = (int)(limit / stage);
     if (S > tc::MAX_STAGES) S = tc::MAX_STAGES;
     if (stages_out) *stages_out = S;

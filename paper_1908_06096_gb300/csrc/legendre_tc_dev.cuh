@@ -209,6 +209,26 @@ struct Geo {
     static constexpr int A_STEP = A_MN ? UK / 8 * 1024 : 32;  // bytes per MMA K step in A
 };
 
+// A GEMM job without its tensor map, as the persistent batch kernel keeps it
+// in shared memory (its maps stay in kernel parameters).
+struct TcLite {
+    const LegGroup *groups;
+    const LegTile *tiles;
+    const char *tab;
+    float *out;
+    int *err;
+    long long ntiles;
+    int ncm, C, Cp, max_nt;
+};
+__device__ __forceinline__ const CUtensorMap *job_map(const TcJob &J, const CUtensorMap *maps, int q)
+{
+    return maps ? &maps[q] : &J.map;
+}
+__device__ __forceinline__ const CUtensorMap *job_map(const TcLite &, const CUtensorMap *maps, int q)
+{
+    return &maps[q];
+}
+
 // Named barrier of the kernel's THREADS threads (warps 0 .. 5): a launch of
 // more warps (the persistent batch kernel) runs the body in its first six.
 __device__ __forceinline__ void tc_sync() { asm volatile("bar.sync 1, %0;" ::"n"(THREADS) : "memory"); }
@@ -217,9 +237,11 @@ __device__ __forceinline__ void tc_sync() { asm volatile("bar.sync 1, %0;" ::"n"
 // kernel parameters or global memory); smem_raw: the dynamic shared memory.
 // relinquish: give up the CTA's right to allocate tensor memory once its
 // columns are held (a CTA that runs the body again must keep it).
+// maps: the jobs' operand tensor maps when B lives in global memory (kernel
+// parameters keep descriptor fetches cheap); null: each job's own.
 template <int KIND, class BATCH>
 __device__ __forceinline__ void leg_tc_body(const BATCH &B, unsigned char *smem_raw, long long cta, long long ncta,
-                                            bool relinquish = true)
+                                            bool relinquish = true, const CUtensorMap *maps = nullptr)
 {
     typedef Geo<KIND> G;
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -274,7 +296,8 @@ __device__ __forceinline__ void leg_tc_body(const BATCH &B, unsigned char *smem_
             bool ok = true;
             for (long long t = cta; ok && t < total; t += ncta) {
                 const int q = find_job<1>(B.prefix, B.njobs, t);
-                const TcJob &J = B.job[q];
+                const auto &J = B.job[q];
+                const CUtensorMap *mp = job_map(J, maps, q);
                 const long long lt_i = t - B.prefix[q];
                 const LegTile lt = J.tiles[lt_i / J.ncm];
                 const int cm = (int)(lt_i % J.ncm);
@@ -298,10 +321,10 @@ __device__ __forceinline__ void leg_tc_body(const BATCH &B, unsigned char *smem_
                         if (G::A_MN) {
 #pragma unroll
                             for (int bx = 0; bx < G::NBOX; ++bx)
-                                tma_load_3d(sa + pl * G::A_PLANE + bx * G::BOX_BYTES, &J.map, cm * TC_M + bx * G::BOX_C,
+                                tma_load_3d(sa + pl * G::A_PLANE + bx * G::BOX_BYTES, mp, cm * TC_M + bx * G::BOX_C,
                                             row, pl, fb);
                         } else {
-                            tma_load_3d(sa + pl * G::A_PLANE, &J.map, row, cm * TC_M, pl, fb);
+                            tma_load_3d(sa + pl * G::A_PLANE, mp, row, cm * TC_M, pl, fb);
                         }
                     }
                     const char *src = J.tab + g.tab_off + (size_t)(lt.ct * g.nkc + kc) * bimg;
@@ -325,7 +348,7 @@ __device__ __forceinline__ void leg_tc_body(const BATCH &B, unsigned char *smem_
             bool any = false;
             for (long long t = cta; ok && t < total; t += ncta, ++local) {
                 const int q = find_job<1>(B.prefix, B.njobs, t);
-                const TcJob &J = B.job[q];
+                const auto &J = B.job[q];
                 const LegTile lt = J.tiles[(t - B.prefix[q]) / J.ncm];
                 const LegGroup g = J.groups[lt.g];
                 const int kc_end = (g.K + G::KC - 1) / G::KC;
@@ -374,7 +397,7 @@ __device__ __forceinline__ void leg_tc_body(const BATCH &B, unsigned char *smem_
         int local = 0;
         for (long long t = cta; t < total; t += ncta, ++local) {
             const int q = find_job<1>(B.prefix, B.njobs, t);
-            const TcJob &J = B.job[q];
+            const auto &J = B.job[q];
             const long long lt_i = t - B.prefix[q];
             const LegTile lt = J.tiles[lt_i / J.ncm];
             const int cm = (int)(lt_i % J.ncm);

@@ -6,6 +6,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 namespace st {
 
 __device__ inline float round_tf32_p(float x)
@@ -40,7 +42,10 @@ __device__ inline void put_op(void *base, long long idx, long long ps, Rr v)
 // column 2 f + (re, im).  One CTA per (m, 32-field tile); smem transpose.
 // One 256-thread block b of job J: warp, lane of the block's own threads,
 // tile 32 x 65 values of shared memory, sync() a barrier of the block.
-template <typename Rr, int S, class SYNC>
+// CH: chunks of 32 degrees moved per round (tile CH x 32 rows), so that a
+// block with few neighbours on its SM keeps more loads in flight.
+// NW: warps of the block (8: 256 threads; fewer for blocks that share a CTA).
+template <typename Rr, int S, int CH = 1, int NW = 8, class SYNC>
 __device__ __forceinline__ void pack_block(const PackJob &J, int b, Rr (*tile)[65], int warp, int lane, SYNC sync)
 {
     const int m = b / J.nft;
@@ -52,29 +57,41 @@ __device__ __forceinline__ void pack_block(const PackJob &J, int b, Rr (*tile)[6
     const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
     const int len = T - m + 1;
     const long long rowE = J.srow[2 * m], rowO = J.srow[2 * m + 1];
-    for (int d0 = 0; d0 < len; d0 += 32) {
-        // load: warp w reads fields w, w+8, ...; lane = d
-        for (int ff = warp; ff < 32; ff += 8) {
-            int fld = f0 + ff, d = d0 + lane;
-            Rr re = 0, im = 0;
-            if (fld < nfields && d < len) {
-                const Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
-                re = a[0];
-                im = m == 0 ? (Rr)0 : a[1];
-                if (J.scale) {
-                    // inverse Laplacian on the unit sphere: -1 / (n (n+1)), 0 at n = 0
-                    const int n = m + d;
-                    const Rr f = n == 0 ? (Rr)0 : (Rr)(-1.0 / ((double)n * (n + 1.0)));
-                    re *= f;
-                    im *= f;
+    typedef typename std::conditional<sizeof(Rr) == 8, double2, float2>::type V2;
+    for (int d0 = 0; d0 < len; d0 += 32 * CH) {
+        // load: warp w reads fields w, w + NW, ... of each chunk (all loads
+        // in flight before the first store); lane = d
+        constexpr int FK = 32 / NW;
+        Rr re[CH][FK], im[CH][FK];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int k = 0; k < FK; ++k) {
+                const int fld = f0 + warp + NW * k, d = d0 + 32 * c + lane;
+                re[c][k] = im[c][k] = 0;
+                if (fld < nfields && d < len) {
+                    const V2 v = *(const V2 *)(spec + ((long long)fld * nspec + q0 + d) * 2);
+                    re[c][k] = v.x;
+                    im[c][k] = m == 0 ? (Rr)0 : v.y;
+                    if (J.scale) {
+                        // inverse Laplacian on the unit sphere: -1 / (n (n+1)), 0 at n = 0
+                        const int n = m + d;
+                        const Rr f = n == 0 ? (Rr)0 : (Rr)(-1.0 / ((double)n * (n + 1.0)));
+                        re[c][k] *= f;
+                        im[c][k] *= f;
+                    }
                 }
             }
-            tile[lane][2 * ff] = re;
-            tile[lane][2 * ff + 1] = im;
-        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int k = 0; k < FK; ++k) {
+                tile[32 * c + lane][2 * (warp + NW * k)] = re[c][k];
+                tile[32 * c + lane][2 * (warp + NW * k) + 1] = im[c][k];
+            }
         sync();
-        // store: warp w writes rows d = w, w+8, ...; lanes cover 64 columns
-        for (int dd = warp; dd < 32; dd += 8) {
+        // store: warp w writes rows d = w, w + NW, ...; lanes cover 64 columns
+        for (int dd = warp; dd < 32 * CH; dd += NW) {
             int d = d0 + dd;
             if (d >= len) continue;
             long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
@@ -89,7 +106,7 @@ __device__ __forceinline__ void pack_block(const PackJob &J, int b, Rr (*tile)[6
 
 // Operand rows (direct GEMM output, FP32/FP64) -> spectra.  Wavenumbers kept
 // by no row (m > max_m) are written as zero; Im a_n^0 is written as zero.
-template <typename Rr, class SYNC>
+template <typename Rr, int CH = 1, int NW = 8, class SYNC>
 __device__ __forceinline__ void unpack_block(const PackJob &J, int b, Rr (*tile)[65], int warp, int lane, SYNC sync)
 {
     const int m = b / J.nft;
@@ -102,24 +119,40 @@ __device__ __forceinline__ void unpack_block(const PackJob &J, int b, Rr (*tile)
     const int len = T - m + 1;
     const long long rowE = J.srow[2 * m], rowO = J.srow[2 * m + 1];
     const bool zero = m > J.max_m;
-    for (int d0 = 0; d0 < len; d0 += 32) {
-        for (int dd = warp; dd < 32; dd += 8) {
-            int d = d0 + dd;
-            long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
-            for (int cc = lane; cc < 64; cc += 32) {
-                int c = 2 * f0 + cc;
-                Rr v = 0;
-                if (!zero && d < len && c < 2 * nfields) v = in[row * Cp + c];
-                tile[dd][cc] = v;
+    for (int d0 = 0; d0 < len; d0 += 32 * CH) {
+        // rows d = w, w+8, ... of each chunk; all loads in flight first
+        constexpr int DK = 32 / NW;
+        Rr v[CH][DK][2];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int k = 0; k < DK; ++k) {
+                const int d = d0 + 32 * c + warp + NW * k;
+                const long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = 2 * f0 + lane + 32 * h;
+                    v[c][k][h] = 0;
+                    if (!zero && d < len && col < 2 * nfields) v[c][k][h] = in[row * Cp + col];
+                }
             }
-        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int k = 0; k < DK; ++k)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) tile[32 * c + warp + NW * k][lane + 32 * h] = v[c][k][h];
         sync();
-        for (int ff = warp; ff < 32; ff += 8) {
-            int fld = f0 + ff, d = d0 + lane;
-            if (fld < nfields && d < len) {
-                Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
-                a[0] = tile[lane][2 * ff];
-                a[1] = m == 0 ? (Rr)0 : tile[lane][2 * ff + 1];
+        for (int ff = warp; ff < 32; ff += NW) {
+            const int fld = f0 + ff;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int d = d0 + 32 * c + lane;
+                if (fld < nfields && d < len) {
+                    Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
+                    a[0] = tile[32 * c + lane][2 * ff];
+                    a[1] = m == 0 ? (Rr)0 : tile[32 * c + lane][2 * ff + 1];
+                }
             }
         }
         sync();

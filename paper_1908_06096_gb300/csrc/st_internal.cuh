@@ -437,8 +437,10 @@ st_status launch_tc_jobs(int prec, const TcJob *jobs, int n, int sm_count, cudaS
                          unsigned long long wait_ns = 2000000000ull);
 
 // ---- persistent batch kernel (batch_persistent.cu) ----
-// The stage jobs of one precision group of a batch; fft jobs built for
-// 512-thread CTAs (fft_jobs with kb = twice the plan's per-CTA budget).
+// Shared memory of each half of its CTA in the row-FFT stages.
+constexpr int FF_HALF_BYTES = 110 * 1024;
+// The stage jobs of one precision group of a batch; fft jobs built within
+// FF_HALF_BYTES of shared memory a CTA.
 struct PersInput {
     int prec = 0;
     int sm_count = 0;
@@ -451,7 +453,7 @@ struct PersState;
 st_status pers_prepare(const PersInput &in, PersState **out);
 st_status pers_launch(PersState *ps, cudaStream_t s);
 void pers_free(PersState *ps);
-size_t tc_smem_bytes(int prec, int max_nt, int *stages_out);
+size_t tc_smem_bytes(int prec, int max_nt, int *stages_out, size_t cap = 0);
 
 // ---- plan helpers (api.cu) ----
 st_status count_launch(st_plan *p, int kind, cudaStream_t s, const std::function<st_status()> &f);
