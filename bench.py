@@ -453,7 +453,8 @@ def run_ours(args, ws, rank, local):
                                            "fp32": "f32", "fp64": "f64"}[prec],
            "data": "synthetic",
            "config": dict(config_of(wl, prec), launch_shape=dict(zip(
-               ["fft_inv_variant", "fft_inv_kb", "fft_dir_variant", "fft_dir_kb", "legendre_inv_tile"],
+               ["fft_inv_variant", "fft_inv_kb", "fft_dir_variant", "fft_dir_kb", "legendre_inv_tile",
+                "legendre_inv_tile_high_m"],
                plan.launch_shape())), autotuned=not args.no_autotune),
            "roofline": roof, "kernels": kern,
            "e2e": e2e, "gpu_launches": launches, "clocks": ck}

@@ -91,8 +91,9 @@ typedef struct {
     size_t device_bytes;      /* device memory held by the plan */
     size_t table_bytes;       /* of which Legendre tables */
     size_t workspace_bytes;   /* of which workspace */
-    int launch_shape[5];      /* inverse FFT variant, its smem budget (KB), direct FFT variant, its
-                                 budget (KB), inverse Legendre column-tile width (0: automatic) */
+    int launch_shape[6];      /* inverse FFT variant, its smem budget (KB), direct FFT variant, its
+                                 budget (KB), inverse Legendre column-tile width (0: automatic), the
+                                 same for the upper half of the wavenumbers (0: as the former) */
 } st_plan_info;
 
 /*
@@ -126,8 +127,9 @@ st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, 
  * Autotuner (not in the paper).  Times, on this plan and for `nfields`
  * fields, candidate FFT launch shapes (fields per CTA, through the per-CTA
  * shared-memory budget) for each direction and, on tensor-core plans,
- * candidate column-tile widths of the per-m Legendre GEMMs (re-laying out the
- * tables), and keeps the fastest.  Synchronous; allocates a temporary grid buffer.  If cache_path is
+ * candidate column-tile widths of the inverse per-m Legendre GEMMs (re-laying
+ * out the tables), first for all m, then for the upper half of the
+ * wavenumbers on its own, and keeps the fastest.  Synchronous; allocates a temporary grid buffer.  If cache_path is
  * not NULL the choice is appended to that text file; st_plan_create applies a
  * matching entry (same T, grid, precision, field-count bucket and SM count)
  * from the file named by the ST_TUNE_CACHE environment variable.

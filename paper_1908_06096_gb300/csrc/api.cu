@@ -202,6 +202,13 @@ static void build_groups(st_plan *p, int dir)
         nt_inv = std::min(p->nt_inv, (J + 15) / 16 * 16);
         nct_inv = (J + nt_inv - 1) / nt_inv;
     }
+    // wavenumbers of the upper half (shorter reductions) may take their own width
+    const int m_split = (p->max_m + 1) / 2;
+    int nt_hi = nt_inv, nct_hi = nct_inv;
+    if (p->nt_inv_hi > 0) {
+        nt_hi = std::min(p->nt_inv_hi, (J + 15) / 16 * 16);
+        nct_hi = (J + nt_hi - 1) / nt_hi;
+    }
 
     std::vector<LegGroup> &G = p->groups_h[dir];
     G.assign(2 * (T + 1), LegGroup{});
@@ -235,8 +242,8 @@ static void build_groups(st_plan *p, int dir)
             }
             if (tc) {
                 if (dir == 0) {
-                    g.nt = nt_inv;
-                    g.nct = nct_inv;
+                    g.nt = m < m_split ? nt_inv : nt_hi;
+                    g.nct = m < m_split ? nct_inv : nct_hi;
                 } else {
                     int n = std::max(g.ncol, 1);
                     g.nct = (n + 255) / 256;
@@ -399,13 +406,14 @@ static void apply_tune_cache(st_plan *p)
     while (fgets(line, sizeof line, f)) {
         std::string l(line);
         if (l.compare(0, key.size() + 1, key + " ") != 0) continue;
-        int v0, k0, v1, k1, nt;
-        if (sscanf(l.c_str() + key.size() + 1, "| %d %d %d %d %d", &v0, &k0, &v1, &k1, &nt) == 5) {
+        int v0, k0, v1, k1, nt, nth = 0;
+        if (sscanf(l.c_str() + key.size() + 1, "| %d %d %d %d %d %d", &v0, &k0, &v1, &k1, &nt, &nth) >= 5) {
             p->fft_var[0] = v0;
             p->fft_kb[0] = k0;
             p->fft_var[1] = v1;
             p->fft_kb[1] = k1;
             p->nt_inv = nt;
+            p->nt_inv_hi = nth;
         }
     }
     fclose(f);
@@ -822,6 +830,7 @@ st_status st_plan_create_shared(st_plan_t *out, st_plan_t base, int max_fields, 
     p->nfast = base->nfast;
     p->fft_var[0] = base->fft_var[0]; p->fft_var[1] = base->fft_var[1];
     p->fft_kb[0] = base->fft_kb[0]; p->fft_kb[1] = base->fft_kb[1]; p->nt_inv = base->nt_inv;
+    p->nt_inv_hi = base->nt_inv_hi;
     for (int d = 0; d < 2; ++d) {
         p->tab[d] = base->tab[d];
         p->tab_bytes[d] = base->tab_bytes[d];
@@ -872,6 +881,7 @@ st_status st_plan_query(st_plan_t p, st_plan_info *info)
     info->launch_shape[2] = p->fft_var[1];
     info->launch_shape[3] = p->fft_kb[1];
     info->launch_shape[4] = p->nt_inv;
+    info->launch_shape[5] = p->nt_inv_hi;
     return ST_OK;
 }
 

@@ -352,6 +352,7 @@ struct st_plan {
     int fft_var[2] = {0, 0};       // FFT launch variant (threads per CTA, CTAs per SM)
     int fft_kb[2] = {100, 100};    // FFT shared-memory budget per CTA (KB): fields per CTA
     int nt_inv = 0;                // inverse Legendre column-tile width (0: automatic)
+    int nt_inv_hi = 0;             // the same for m >= (max_m + 1) / 2 (0: as nt_inv)
 
     // fault injection (tests): the next tensor-core Legendre launch withholds
     // its operand copies and bounds its waits by inject_wait_ns

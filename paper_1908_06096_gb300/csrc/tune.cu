@@ -3,7 +3,10 @@
 //  - FFT, per direction: the shared-memory budget per CTA, which sets how
 //    many fields a CTA holds (FP32 plans).
 //  - Tensor-core Legendre: the inverse column-tile width (the tile shape of
-//    the per-m GEMMs; changing it re-lays out the tables).
+//    the per-m GEMMs; changing it re-lays out the tables), first for all m,
+//    then for the upper half of the wavenumbers alone (their reductions are
+//    shorter, so a different width can suit them).  The direct GEMMs take
+//    one column tile per (m, parity) up to 256 columns by construction.
 // The choice can be appended to a cache file; st_plan_create applies a
 // matching entry from the file named by ST_TUNE_CACHE.
 #include "st_internal.cuh"
@@ -85,8 +88,21 @@ extern "C" st_status st_plan_autotune(st_plan_t p, int nfields, const char *cach
             if ((r = time_ms(s, reps, [&] { return launch_leg_tc(p, 0, nfields, s); }, &ms)) != ST_OK) break;
             if (ms < best) { best = ms; bnt = nt; }
         }
+        p->nt_inv = bnt;
+        // then the upper half of the wavenumbers alone
+        int bhi = 0;
+        for (int nt : cand) {
+            if (r != ST_OK) break;
+            if (nt > jmax && nt != cand[0]) continue;
+            if (nt == bnt) continue;  // the width chosen for all m is timed already
+            p->nt_inv_hi = nt;
+            if ((r = rebuild_legendre(p, s)) != ST_OK) break;
+            float ms = 0;
+            if ((r = time_ms(s, reps, [&] { return launch_leg_tc(p, 0, nfields, s); }, &ms)) != ST_OK) break;
+            if (ms < best) { best = ms; bhi = nt; }
+        }
         if (r == ST_OK) {
-            p->nt_inv = bnt;
+            p->nt_inv_hi = bhi;
             r = rebuild_legendre(p, s);
         }
     }
@@ -95,8 +111,8 @@ extern "C" st_status st_plan_autotune(st_plan_t p, int nfields, const char *cach
     if (r == ST_OK && cache_path && *cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s | %d %d %d %d %d\n", tune_key(p, nfields).c_str(), p->fft_var[0], p->fft_kb[0],
-                    p->fft_var[1], p->fft_kb[1], p->nt_inv);
+            fprintf(f, "%s | %d %d %d %d %d %d\n", tune_key(p, nfields).c_str(), p->fft_var[0], p->fft_kb[0],
+                    p->fft_var[1], p->fft_kb[1], p->nt_inv, p->nt_inv_hi);
             fclose(f);
         }
     }

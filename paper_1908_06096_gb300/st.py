@@ -38,7 +38,7 @@ class _PlanInfo(ctypes.Structure):
                 ("spec_elems", ctypes.c_size_t), ("grid_points", ctypes.c_size_t),
                 ("element_bytes", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t),
                 ("table_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
-                ("launch_shape", ctypes.c_int * 5)]
+                ("launch_shape", ctypes.c_int * 6)]
 
 
 class _BatchItem(ctypes.Structure):
