@@ -57,38 +57,60 @@ __device__ __forceinline__ void pack_block(const PackJob &J, int b, Rr (*tile)[6
     const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
     const int len = T - m + 1;
     const long long rowE = J.srow[2 * m], rowO = J.srow[2 * m + 1];
-    typedef typename std::conditional<sizeof(Rr) == 8, double2, float2>::type V2;
     for (int d0 = 0; d0 < len; d0 += 32 * CH) {
-        // load: warp w reads fields w, w + NW, ... of each chunk (all loads
-        // in flight before the first store); lane = d
-        constexpr int FK = 32 / NW;
-        Rr re[CH][FK], im[CH][FK];
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-#pragma unroll
-            for (int k = 0; k < FK; ++k) {
-                const int fld = f0 + warp + NW * k, d = d0 + 32 * c + lane;
-                re[c][k] = im[c][k] = 0;
+        if constexpr (CH == 1 && NW == 8) {
+            // a full 256-thread block: load and stage field by field (its
+            // neighbours on the SM hide the latency)
+            for (int ff = warp; ff < 32; ff += 8) {
+                const int fld = f0 + ff, d = d0 + lane;
+                Rr re = 0, im = 0;
                 if (fld < nfields && d < len) {
-                    const V2 v = *(const V2 *)(spec + ((long long)fld * nspec + q0 + d) * 2);
-                    re[c][k] = v.x;
-                    im[c][k] = m == 0 ? (Rr)0 : v.y;
+                    const Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
+                    re = a[0];
+                    im = m == 0 ? (Rr)0 : a[1];
                     if (J.scale) {
                         // inverse Laplacian on the unit sphere: -1 / (n (n+1)), 0 at n = 0
                         const int n = m + d;
                         const Rr f = n == 0 ? (Rr)0 : (Rr)(-1.0 / ((double)n * (n + 1.0)));
-                        re[c][k] *= f;
-                        im[c][k] *= f;
+                        re *= f;
+                        im *= f;
                     }
                 }
+                tile[lane][2 * ff] = re;
+                tile[lane][2 * ff + 1] = im;
             }
+        } else {
+            // load: warp w reads fields w, w + NW, ... of each chunk (all loads
+            // in flight before the first store); lane = d
+            constexpr int FK = 32 / NW;
+            Rr re[CH][FK], im[CH][FK];
 #pragma unroll
-        for (int c = 0; c < CH; ++c)
+            for (int c = 0; c < CH; ++c)
 #pragma unroll
-            for (int k = 0; k < FK; ++k) {
-                tile[32 * c + lane][2 * (warp + NW * k)] = re[c][k];
-                tile[32 * c + lane][2 * (warp + NW * k) + 1] = im[c][k];
-            }
+                for (int k = 0; k < FK; ++k) {
+                    const int fld = f0 + warp + NW * k, d = d0 + 32 * c + lane;
+                    re[c][k] = im[c][k] = 0;
+                    if (fld < nfields && d < len) {
+                        const Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
+                        re[c][k] = a[0];
+                        im[c][k] = m == 0 ? (Rr)0 : a[1];
+                        if (J.scale) {
+                            // inverse Laplacian on the unit sphere: -1 / (n (n+1)), 0 at n = 0
+                            const int n = m + d;
+                            const Rr f = n == 0 ? (Rr)0 : (Rr)(-1.0 / ((double)n * (n + 1.0)));
+                            re[c][k] *= f;
+                            im[c][k] *= f;
+                        }
+                    }
+                }
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+                for (int k = 0; k < FK; ++k) {
+                    tile[32 * c + lane][2 * (warp + NW * k)] = re[c][k];
+                    tile[32 * c + lane][2 * (warp + NW * k) + 1] = im[c][k];
+                }
+        }
         sync();
         // store: warp w writes rows d = w, w + NW, ...; lanes cover 64 columns
         for (int dd = warp; dd < 32 * CH; dd += NW) {
