@@ -479,28 +479,66 @@ __device__ __forceinline__ int raw_at(int f, int SL) { return (f * SL + 1) & ~1;
 // cz holds the thread's R1 chirp factors (ones on mode-0 rows), loaded once
 // for all fields.
 template <class PL>
-__device__ __forceinline__ void stage1_raw(C *x, int G, const C *__restrict__ tw, int N, const C *cz)
+__device__ __forceinline__ void stage1_raw(C *x, int G, const C *__restrict__ tw, int N, const C *cz,
+                                           const C *__restrict__ chirp, bool blue)
 {
     constexpr int L = PL::L, R = PL::template R<1>(), ST = L / R, SL = PL::SL;
-    static_assert(ST <= NT, "one stage-1 item per thread per field");
     const int n = FF_TID;
-    for (int f = 0; f < G; ++f) {
-        const float *raw = (const float *)(x + raw_at(f, SL));
-        C v[R];
-        if (n < ST) {
+    if constexpr (ST <= NT) {
+        // one item per thread per field; cz holds the thread's R chirp
+        // factors (ones on mode-0 rows), loaded once for all fields
+        for (int f = 0; f < G; ++f) {
+            const float *raw = (const float *)(x + raw_at(f, SL));
+            C v[R];
+            if (n < ST) {
 #pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int e = n + q * ST;
-                v[q] = e < N ? cmul(cz[q], make_float2(raw[e], raw[N + e])) : make_float2(0.f, 0.f);
+                for (int q = 0; q < R; ++q) {
+                    const int e = n + q * ST;
+                    v[q] = e < N ? cmul(cz[q], make_float2(raw[e], raw[N + e])) : make_float2(0.f, 0.f);
+                }
+            }
+            FF_SYNC();
+            if (n < ST) {
+                dft<R>(v);
+                twiddle_pow<R>(v, tw[n]);
+                C *xf = x + f * SL;
+#pragma unroll
+                for (int q = 0; q < R; ++q) xf[slot_of<ST, R>(n, q)] = v[q];
             }
         }
-        FF_SYNC();
-        if (n < ST) {
-            dft<R>(v);
-            twiddle_pow<R>(v, tw[n]);
+    } else {
+        // ST / NT items per thread per field, all read before the barrier;
+        // the chirp factors are loaded per field, ahead of the reads
+        static_assert(ST % NT == 0, "whole items per thread");
+        constexpr int IT = ST / NT;
+        for (int f = 0; f < G; ++f) {
+            const float *raw = (const float *)(x + raw_at(f, SL));
+            C v[IT][R];
+#pragma unroll
+            for (int i = 0; i < IT; ++i)
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int e = n + i * NT + q * ST;
+                    v[i][q] = make_float2(1.f, 0.f);
+                    if (blue && e < N) v[i][q] = __ldg(&chirp[e]);
+                }
+#pragma unroll
+            for (int i = 0; i < IT; ++i)
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const int e = n + i * NT + q * ST;
+                    v[i][q] = e < N ? cmul(v[i][q], make_float2(raw[e], raw[N + e])) : make_float2(0.f, 0.f);
+                }
+            FF_SYNC();
             C *xf = x + f * SL;
 #pragma unroll
-            for (int q = 0; q < R; ++q) xf[slot_of<ST, R>(n, q)] = v[q];
+            for (int i = 0; i < IT; ++i) {
+                const int ni = n + i * NT;
+                dft<R>(v[i]);
+                twiddle_pow<R>(v[i], tw[ni]);
+#pragma unroll
+                for (int q = 0; q < R; ++q) xf[slot_of<ST, R>(ni, q)] = v[i][q];
+            }
         }
     }
 }
@@ -619,7 +657,8 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
     // Rows whose offsets, length and field stride are multiples of four
     // floats arrive by bulk copies into the fields' slots (one per row and
     // field, tracked by one barrier) instead of per-thread loads.
-    constexpr bool kRawFits = PL::L / PL::template R<1>() <= NT;
+    constexpr int kST1 = PL::L / PL::template R<1>();
+    constexpr bool kRawFits = kST1 <= NT || kST1 % NT == 0;
     const bool raw = kRawFits && G > 0 && ((on | os | (long long)N | npts) & 3) == 0 &&
                      (reinterpret_cast<uintptr_t>(J.src) & 15) == 0 && (smem_addr(x) & 15) == 0;
     if (raw) {
@@ -646,7 +685,7 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
         for (int q = 0; q < R1; ++q) {
             const int e = FF_TID + q * ST1;
             cz[q] = make_float2(1.f, 0.f);
-            if (blue && FF_TID < ST1 && e < N) cz[q] = __ldg(&chirp[e]);
+            if (ST1 <= NT && blue && FF_TID < ST1 && e < N) cz[q] = __ldg(&chirp[e]);
         }
         cp_async_wait_all();
         bar_wait(bar, 0, &abort_raw);
@@ -665,7 +704,7 @@ __device__ __noinline__ void dir_body(const FftJob &J, const RowPair &rp, int f0
             }
             return;
         }
-        if constexpr (kRawFits) stage1_raw<PL>(x, G, tw, N, cz);
+        if constexpr (kRawFits) stage1_raw<PL>(x, G, tw, N, cz, chirp, blue);
     } else {
         stage1_in<PL>(x, G, twg, [&](int f, int e, int) -> C {
             C z = make_float2(0.f, 0.f);
