@@ -76,16 +76,7 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
                (p->rowpairs_h[p->row_order[e]].mode == 1) == blue)
             ++e;
         const size_t tab = (size_t)ff_table_elems(id) * cs;
-        // the inverse stages each field's S, A values (8 bytes per (m,
-        // parity)) behind the table: 16 (mtop + 1) bytes a field, mtop the
-        // run's largest staged wavenumber
-        int mtop = 0;
-        for (int q = r; q < e; ++q) {
-            const RowPair &x = p->rowpairs_h[p->row_order[q]];
-            mtop = std::max(mtop, blue ? x.M : x.N / 2);
-        }
-        const size_t stage_per_field = dir == 0 ? 16 * (size_t)(mtop + 1) : 0;
-        int G = (int)std::min<size_t>(budget > tab ? (budget - tab) / ((size_t)SL * cs + stage_per_field) : 1, 128);
+        int G = (int)std::min<size_t>(budget > tab ? (budget - tab) / ((size_t)SL * cs) : 1, 128);
         G = std::max(1, std::min(G, nfields));
         if (G > 1 && (G & 1)) --G;
         FftJob J1 = base;
@@ -96,8 +87,7 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
         J1.G = G;
         J1.Sslot = SL;
         J1.nfg = (nfields + G - 1) / G;
-        J1.smem = (int)((size_t)((G * SL + 1) & ~1) * cs + tab +
-                        (dir == 0 ? 32 * (size_t)(mtop + 1) * ((G + 1) / 2) : 0));
+        J1.smem = (int)((size_t)((G * SL + 1) & ~1) * cs + tab);
         if (J1.smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
         jobs.push_back(J1);
         r = e;

@@ -265,13 +265,6 @@ __device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
                  "l"(gsrc)
                  : "memory");
 }
-// 16 bytes, global -> shared, not kept in L1 (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
-                 "l"(gsrc)
-                 : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -820,74 +813,77 @@ __device__ __noinline__ void inv_body(const FftJob &J, const RowPair &rp, int f0
     const int Cp = J.Cp, Jp = J.Jp, T = J.T, j = rp.j;
 
 
-    // The S, A values of this row and these fields (16 bytes per (m, parity)
-    // for two fields, 8 for one), scattered over the Fourier buffer, first
-    // land in a staging area behind the twiddle table by asynchronous copies
-    // issued all at once; then they are combined into the slots.
+    // staging: Bluestein rows keep the inputs at their natural places (0 .. M
+    // and L - M .. L - 1, the rest is zero by index in stage 1); mode-0 rows
+    // run DIT passes only, so every place 0 .. N - 1 is written, in the
+    // digit-reversed order.
     const int G2 = (G + 1) >> 1;
     const int mtop = blue ? M : N / 2;
+    // four items per thread per round: every global load of the round is
+    // issued before the first is used
     const int nitems = (mtop + 1) * G2;
-    float4 *stg = (float4 *)(tws + (PL::TW_SMEM ? PL::TWN : 0));
-    for (int idx = FF_TID; idx < nitems; idx += NT) {
-        const int m = idx / G2, f = 2 * (idx - m * G2);
-        float4 *d = stg + 2 * idx;
-        if (m <= M) {
-            const bool two = f + 1 < G;
-            const long long rS = ((long long)m * Jp + j) * Cp + 2 * (f0 + f);
-            const long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * (f0 + f);
-            // The odd-parity half of m = T is empty (no n = T + 1): A = 0 there.
-            const bool hasA = m < T || J.a_top;
-            if (two) {
-                cp_async16(d, fb + rS);
-                if (hasA) cp_async16(d + 1, fb + rA);
-                else d[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                cp_async8(d, fb + rS);
-                if (hasA) cp_async8(d + 1, fb + rA);
-                else d[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        } else {
-            d[0] = d[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-    cp_async_commit();
-    cp_async_wait_all();
-    FF_SYNC();
-
-    // Bluestein rows keep the inputs at their natural places (0 .. M and
-    // L - M .. L - 1, the rest is zero by index in stage 1); mode-0 rows run
-    // DIT passes only, so every place 0 .. N - 1 is written, in the
-    // digit-reversed order.
-    for (int idx = FF_TID; idx < nitems; idx += NT) {
-        const int m = idx / G2, f = 2 * (idx - m * G2);
-        const bool two = f + 1 < G;
-        const float4 sv = stg[2 * idx], av = stg[2 * idx + 1];
-        C cw = make_float2(1.f, 0.f);
-        if (blue && m <= M) cw = __ldg(&chirp[m]);  // w_{-m} = w_m
-        const int pa = blue ? m : dif_place<PL>(m);
-        const int pb = blue ? L - m : dif_place<PL>(N - m);
+    for (int base = FF_TID; base < nitems; base += 4 * NT) {
+        float4 sv[4], av[4];
+        C cw[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1 && !two) break;
-            const float sx = h ? sv.z : sv.x, sy = h ? sv.w : sv.y;
-            const float ax = h ? av.z : av.x, ay = h ? av.w : av.y;
-            const float nx = sx + ax, ny = sy + ay;  // north F_m
-            const float qx = sx - ax, qy = sy - ay;  // south F_m
-            C *xf = x + (f + h) * SL;
-            if (m == 0) {
-                C v = make_float2(nx, -qx);
-                if (blue) v = cmul(v, cw);
-                xf[sw(pa)] = v;
-            } else {
-                C a = make_float2(nx - qy, -(ny + qx));
-                C bb = make_float2(nx + qy, ny - qx);
-                if (blue) {
-                    a = cmul(a, cw);
-                    bb = cmul(bb, cw);
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * NT;
+            const int m = idx / G2, f = 2 * (idx - m * G2);
+            sv[u] = av[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            cw[u] = make_float2(1.f, 0.f);
+            if (idx < nitems && m <= M) {
+                const bool two = f + 1 < G;
+                const long long rS = ((long long)m * Jp + j) * Cp + 2 * (f0 + f);
+                const long long rA = (((long long)(T + 1) + m) * Jp + j) * Cp + 2 * (f0 + f);
+                // two fields: 16-byte loads (f0 + f is even then); one: 8 bytes.
+                // The odd-parity half of m = T is empty (no n = T + 1): A = 0 there.
+                if (two) {
+                    sv[u] = *(const float4 *)(fb + rS);
+                    if (m < T || J.a_top) av[u] = *(const float4 *)(fb + rA);
+                } else {
+                    const float2 s2 = *(const float2 *)(fb + rS);
+                    sv[u].x = s2.x;
+                    sv[u].y = s2.y;
+                    if (m < T || J.a_top) {
+                        const float2 a2 = *(const float2 *)(fb + rA);
+                        av[u].x = a2.x;
+                        av[u].y = a2.y;
+                    }
                 }
-                xf[sw(pa)] = a;
-                // m = N / 2 (zero beyond M) maps to one place on mode-0 rows
-                if (!(pa == pb)) xf[sw(pb)] = bb;
+                if (blue) cw[u] = __ldg(&chirp[m]);  // w_{-m} = w_m
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int idx = base + u * NT;
+            if (idx >= nitems) break;
+            const int m = idx / G2, f = 2 * (idx - m * G2);
+            const bool two = f + 1 < G;
+            const int pa = blue ? m : dif_place<PL>(m);
+            const int pb = blue ? L - m : dif_place<PL>(N - m);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !two) break;
+                const float sx = h ? sv[u].z : sv[u].x, sy = h ? sv[u].w : sv[u].y;
+                const float ax = h ? av[u].z : av[u].x, ay = h ? av[u].w : av[u].y;
+                const float nx = sx + ax, ny = sy + ay;  // north F_m
+                const float qx = sx - ax, qy = sy - ay;  // south F_m
+                C *xf = x + (f + h) * SL;
+                if (m == 0) {
+                    C v = make_float2(nx, -qx);
+                    if (blue) v = cmul(v, cw[u]);
+                    xf[sw(pa)] = v;
+                } else {
+                    C a = make_float2(nx - qy, -(ny + qx));
+                    C bb = make_float2(nx + qy, ny - qx);
+                    if (blue) {
+                        a = cmul(a, cw[u]);
+                        bb = cmul(bb, cw[u]);
+                    }
+                    xf[sw(pa)] = a;
+                    // m = N / 2 (zero beyond M) maps to one place on mode-0 rows
+                    if (!(pa == pb)) xf[sw(pb)] = bb;
+                }
             }
         }
     }
