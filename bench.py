@@ -555,7 +555,8 @@ def mixed_batch(args, dev):
     staged = [out.clone() for (_, _, _, _, out) in items]
     try:
         ms_pers = timed(persistent=True)
-        same = all(torch.equal(a, out) for a, (_, _, _, _, out) in zip(staged, items))
+        same = max(float(((a - out).abs().max() / a.abs().max()).item())
+                   for a, (_, _, _, _, out) in zip(staged, items))
         pers_note = None
     except st.STError as e:
         ms_pers, same, pers_note = None, None, str(e)
@@ -577,7 +578,7 @@ def mixed_batch(args, dev):
     return {"requests": len(reqs), "fields": fields, "ms_per_batch": ms,
             "field_transforms_per_s": fields / (ms * 1e-3),
             "ms_per_batch_persistent": ms_pers, "ms_per_batch_staged_graph": ms_graph,
-            "persistent_equals_staged_bitwise": same, "persistent_unavailable": pers_note,
+            "persistent_vs_staged_max_rel": same, "persistent_unavailable": pers_note,
             "kernel_launches_per_run": {"persistent": 1 if ms_pers is not None else None,
                                         "staged_graph": "one per stage and FFT plan group"},
             "ms_one_call_per_request": ms_seq,

