@@ -413,7 +413,30 @@ __device__ __forceinline__ void leg_tc_body(const BATCH &B, unsigned char *smem_
             const int col0 = lt.ct * g.nt;
             const uint32_t taddr = tmem_base + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
             float *o = J.out + g.out_row0 * (long long)J.Cp + c;
-            for (int j0 = 0; j0 < g.nt; j0 += 16) {
+            // the tile's columns that hold data (a group's last tile may be
+            // partial), 32 a round: two loads from tensor memory in flight
+            // before the wait
+            const int jend = min(g.nt, (g.ncol - col0 + 15) & ~15);
+            int j0 = 0;
+            for (; j0 + 32 <= jend; j0 += 32) {
+                uint32_t ra[16], rb[16];
+                tmem_ld16(taddr + (uint32_t)j0, ra);
+                tmem_ld16(taddr + (uint32_t)(j0 + 16), rb);
+                tmem_ld_wait();
+                if (c < J.C) {
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int col = col0 + j0 + u;
+                        if (col < g.ncol) o[(long long)col * J.Cp] = __uint_as_float(ra[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int col = col0 + j0 + 16 + u;
+                        if (col < g.ncol) o[(long long)col * J.Cp] = __uint_as_float(rb[u]);
+                    }
+                }
+            }
+            if (j0 < jend) {
                 uint32_t r[16];
                 tmem_ld16(taddr + (uint32_t)j0, r);
                 tmem_ld_wait();
