@@ -293,10 +293,10 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n);
  * cooperative launch, one CTA per SM looping over every request's work of
  * each stage in turn, with bounded grid-wide barriers between the stages (a
  * barrier that gives up sets bit 16 in the error word of the first item's
- * plan, reported by st_plan_sync as ST_ERR_TIMEOUT).  Mode 2 takes batches
- * of one tensor-core precision (BF16x3 or 3xTF32), at most 64 items a
- * direction, whose rows all have compile-time FFT plans of length up to 4096
- * (truncations up to T639 on octahedral grids); any other batch returns
+ * plan, reported by st_plan_sync as ST_ERR_TIMEOUT).  Mode 2 takes BF16x3
+ * batches of at most 64 items a direction whose rows all have compile-time
+ * FFT plans of length up to 4096 (truncations up to T639 on octahedral
+ * grids); any other batch returns
  * ST_ERR_UNSUPPORTED with the reason in st_last_error.  Modes 0 and 1 give
  * the same results bit for bit; mode 2 agrees with them to within the last
  * bits (its row-FFT bodies are separately compiled instances of the same

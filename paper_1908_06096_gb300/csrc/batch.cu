@@ -19,6 +19,7 @@ struct st_batch {
         std::vector<long long> simt_inv_blocks, simt_dir_blocks;
         std::vector<FftJob> fft_inv, fft_dir;
         std::vector<FftJob> fft_inv_w, fft_dir_w;  // the same rows within a half CTA's shared memory
+        std::vector<std::pair<st_plan *, int>> tf32_dir;  // 3xTF32 direct items: operand transposes
         size_t smem_inv = 0, smem_dir = 0;
         int var_inv = 0, var_dir = 0;  // launch variant of the largest job
         long long big_inv = -1, big_dir = -1;
@@ -79,6 +80,8 @@ st_status batch_launch(st_batch *b, cudaStream_t s)
                  return launch_fft_jobs(1, prec, j, n, S.smem_dir, s, S.var_dir);
              })))
             return r;
+        for (auto &pn : S.tf32_dir)
+            if ((r = launch_fb_tf32split(pn.first, pn.second, s))) return r;
         if ((r = chunked(S.tc_dir, [&](const TcJob *j, int n, size_t) { return launch_tc_jobs(prec, j, n, b->sm_count, s); })))
             return r;
         if ((r = chunked(S.simt_dir, [&](const SimtJob *j, int n, size_t i) {
@@ -193,12 +196,13 @@ st_status st_batch_create(st_batch_t *out, const st_batch_item *items, int n)
         if (it.direction != 0) {
             std::vector<FftJob> fj;
             size_t smem = 0;
-            if ((r = fft_jobs(p, 1, it.nfields, it.grid, p->fbop, fj, &smem))) { delete b; return r; }
+            if ((r = fft_dir_jobs(p, it.nfields, it.grid, fj, &smem))) { delete b; return r; }
             S.fft_dir.insert(S.fft_dir.end(), fj.begin(), fj.end());
+            if (p->prec == P_TF32X3) S.tf32_dir.emplace_back(p, it.nfields);
             if (p->prec != P_FP64) {
                 std::vector<FftJob> fw;
                 size_t sw = 0;
-                if (fft_jobs(p, 1, it.nfields, it.grid, p->fbop, fw, &sw, wide_kb(p, 1)) == ST_OK)
+                if (fft_dir_jobs(p, it.nfields, it.grid, fw, &sw, wide_kb(p, 1)) == ST_OK)
                     S.fft_dir_w.insert(S.fft_dir_w.end(), fw.begin(), fw.end());
                 else
                     S.fft_dir_w.push_back(no_wide_job());

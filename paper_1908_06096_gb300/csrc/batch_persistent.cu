@@ -15,9 +15,10 @@
 // bounded: past two seconds the CTA records bit 16 in the error word of the
 // batch's first plan and every CTA leaves at its next barrier.
 //
-// Scope: one precision of the tensor-core forms (BF16x3 or 3xTF32), at most
-// 64 items a direction, every row on a compile-time FFT plan of groups 0 and
-// 1 (lengths up to 4096, truncations up to T639 on octahedral grids).  Other
+// Scope: BF16x3 batches (the 3xTF32 direct operand needs a transpose after
+// the row FFTs, which this kernel does not run), at most 64 items a
+// direction, every row on a compile-time FFT plan of groups 0 and 1
+// (lengths up to 4096, truncations up to T639 on octahedral grids).  Other
 // batches are refused with ST_ERR_UNSUPPORTED and run per stage.
 #include "legendre_tc_dev.cuh"
 #include "pack_dev.cuh"
@@ -321,8 +322,8 @@ st_status tc_view(int prec, const std::vector<TcJob> &jobs, pers::TcView *B, siz
 st_status pers_prepare(const PersInput &in, PersState **out)
 {
     *out = nullptr;
-    if (in.prec != P_BF16X3 && in.prec != P_TF32X3) {
-        set_last_error("the persistent batch kernel runs BF16x3 and 3xTF32 batches only");
+    if (in.prec != P_BF16X3) {
+        set_last_error("the persistent batch kernel runs BF16x3 batches only");
         return ST_ERR_UNSUPPORTED;
     }
     if (in.tc_inv.size() > (size_t)MAX_JOBS || in.tc_dir.size() > (size_t)MAX_JOBS) {

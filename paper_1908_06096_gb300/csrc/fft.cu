@@ -169,13 +169,72 @@ st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_
     return ST_ERR_ARG;
 }
 
+// The 3xTF32 direct GEMM reads its data operand K-major (latitude rows
+// contiguous per data column), which a row FFT, one latitude row pair per
+// CTA, could only write four bytes at a time.  So the row FFTs of 3xTF32
+// plans write E/O row-major in FP32 into the plan's inverse Fourier buffer
+// (free during a direct transform), and this kernel transposes 32 x 32
+// tiles into the split operand: hi = tf32(v), lo = tf32(v - hi), column c
+// of each plane at c Rp + r.  Rows the row FFTs did not write carry older
+// finite values, which meet zero table entries in the GEMM.
+__global__ void __launch_bounds__(256) k_fb_tf32split(const float *__restrict__ src, float *__restrict__ dst,
+                                                      long long rows, int C, int Cp, long long Rp, long long ps)
+{
+    __shared__ float t[32][33];
+    const long long r0 = (long long)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int k = ty; k < 32; k += 8) {
+        const long long r = r0 + k;
+        const int c = c0 + tx;
+        t[k][tx] = (r < rows && c < C) ? src[r * Cp + c] : 0.f;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int c = c0 + k;
+        const long long r = r0 + tx;
+        if (c < C && r < rows) {
+            const float v = t[tx][k];
+            uint32_t h, l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - __uint_as_float(h)));
+            dst[(long long)c * Rp + r] = __uint_as_float(h);
+            dst[(long long)c * Rp + r + ps] = __uint_as_float(l);
+        }
+    }
+}
+
+st_status launch_fb_tf32split(st_plan *p, int nfields, cudaStream_t s)
+{
+    const long long rows = fb_rows(p);
+    const int C = 2 * nfields, Cp = cols_padded(nfields);
+    const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((C + 31) / 32));
+    k_fb_tf32split<<<grid, 256, 0, s>>>((const float *)p->fb, (float *)p->fbop, rows, C, Cp, rows,
+                                       rows * (long long)Cp);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+}
+
+// Jobs of the direct row FFTs of `p` into the operand of its direct GEMM
+// (3xTF32 plans: row-major FP32 into the inverse Fourier buffer, for
+// launch_fb_tf32split).
+st_status fft_dir_jobs(st_plan *p, int nfields, const void *grid, std::vector<FftJob> &jobs, size_t *smem, int kb)
+{
+    const bool tf32 = p->prec == P_TF32X3;
+    st_status r = fft_jobs(p, 1, nfields, grid, tf32 ? p->fb : p->fbop, jobs, smem, kb);
+    if (r == ST_OK && tf32)
+        for (auto &J : jobs) J.smode = S_F32;
+    return r;
+}
+
 st_status launch_fft_dir(st_plan *p, const void *grid, int nfields, cudaStream_t s)
 {
     std::vector<FftJob> jobs;
     size_t smem = 0;
-    st_status r = fft_jobs(p, 1, nfields, grid, p->fbop, jobs, &smem);
+    st_status r = fft_dir_jobs(p, nfields, grid, jobs, &smem);
     if (r) return r;
-    return launch_fft_jobs(1, p->prec, jobs.data(), (int)jobs.size(), smem, s, p->fft_var[1]);
+    if ((r = launch_fft_jobs(1, p->prec, jobs.data(), (int)jobs.size(), smem, s, p->fft_var[1]))) return r;
+    return p->prec == P_TF32X3 ? launch_fb_tf32split(p, nfields, s) : ST_OK;
 }
 
 st_status launch_fft_inv(st_plan *p, void *grid, int nfields, cudaStream_t s, const void *fb_in, int a_top)

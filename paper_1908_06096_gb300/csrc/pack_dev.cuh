@@ -112,14 +112,29 @@ __device__ __forceinline__ void pack_block(const PackJob &J, int b, Rr (*tile)[6
                 }
         }
         sync();
-        // store: warp w writes rows d = w, w + NW, ...; lanes cover 64 columns
-        for (int dd = warp; dd < 32 * CH; dd += NW) {
-            int d = d0 + dd;
-            if (d >= len) continue;
-            long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
-            for (int cc = lane; cc < 64; cc += 32) {
-                int c = 2 * f0 + cc;
-                if (c < 2 * nfields) put_op<S, Rr>(out, op_index(S, row, c, Cp, Rp), ps, tile[dd][cc]);
+        if constexpr (S == S_TF32_SPLIT) {
+            // column-major operand (rows contiguous per column): warp w
+            // writes columns w, w + NW, ...; lanes cover the rows
+            for (int cc = warp; cc < 64; cc += NW) {
+                const int c = 2 * f0 + cc;
+                if (c >= 2 * nfields) continue;
+                for (int dd = lane; dd < 32 * CH; dd += 32) {
+                    const int d = d0 + dd;
+                    if (d >= len) continue;
+                    const long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
+                    put_op<S, Rr>(out, op_index(S, row, c, Cp, Rp), ps, tile[dd][cc]);
+                }
+            }
+        } else {
+            // store: warp w writes rows d = w, w + NW, ...; lanes cover 64 columns
+            for (int dd = warp; dd < 32 * CH; dd += NW) {
+                int d = d0 + dd;
+                if (d >= len) continue;
+                long long row = ((d & 1) ? rowO : rowE) + (d >> 1);
+                for (int cc = lane; cc < 64; cc += 32) {
+                    int c = 2 * f0 + cc;
+                    if (c < 2 * nfields) put_op<S, Rr>(out, op_index(S, row, c, Cp, Rp), ps, tile[dd][cc]);
+                }
             }
         }
         sync();

@@ -403,6 +403,9 @@ const char *kernel_name(const st_plan *p, int kind);
 // ---- job builders and batched launchers ----
 st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst, std::vector<FftJob> &jobs,
                    size_t *smem, int kb = 0);
+st_status fft_dir_jobs(st_plan *p, int nfields, const void *grid, std::vector<FftJob> &jobs, size_t *smem,
+                       int kb = 0);
+st_status launch_fb_tf32split(st_plan *p, int nfields, cudaStream_t s);
 st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s,
                           int variant = 0);
 // fast-kernel launch of n jobs of one group (all jobs' kind == group), one direction
