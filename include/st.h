@@ -308,7 +308,7 @@ st_status st_batch_destroy(st_batch_t batch);
  * Per-kernel timing (not in the paper; a measurement aid).  While enabled,
  * every kernel the plan launches is bracketed by two CUDA events recorded on
  * its launch stream; st_plan_timings waits for them and reports, per kernel,
- * the number of launches and the summed event time since the last reset.
+ * the number of kernel launches and the summed event time since the last reset.
  * Do not enable timing while capturing the plan's calls into a CUDA graph.
  * Launch counts are kept whether or not timing is enabled.
  */

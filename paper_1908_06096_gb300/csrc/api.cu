@@ -678,8 +678,14 @@ static cudaEvent_t take_event(st_plan *p)
     return e;
 }
 
-// Runs one launcher, counting it and, when timing is on, bracketing it with
-// events on its stream.
+int &kernel_launches()
+{
+    static thread_local int n = 0;
+    return n;
+}
+
+// Runs one launcher, counting the kernels it launches and, when timing is
+// on, bracketing it with events on its stream.
 template <class F>
 static st_status counted(st_plan *p, int kind, cudaStream_t s, F f)
 {
@@ -689,8 +695,9 @@ static st_status counted(st_plan *p, int kind, cudaStream_t s, F f)
         b = take_event(p);
         if (a) cudaEventRecord(a, s);
     }
+    const int k0 = kernel_launches();
     st_status r = f();
-    if (r == ST_OK) p->launches[kind]++;
+    if (r == ST_OK) p->launches[kind] += kernel_launches() - k0;
     if (p->timing && a && b) {
         cudaEventRecord(b, s);
         p->pending.push_back({kind, a, b});

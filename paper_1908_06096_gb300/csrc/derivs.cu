@@ -78,6 +78,7 @@ st_status launch_deriv_combine(st_plan *p, int mode, int nfields, void *fb, cons
     else
         k_deriv_combine<float><<<(unsigned)blocks, threads, 0, s>>>((float *)fb, (const float *)fb2, nrows, p->T,
                                                                     p->Jp, Cp, nfields, mode);
+    ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }
@@ -116,6 +117,7 @@ st_status launch_vordiv_combine(st_plan *p, int nfields, void *sout, const void 
     else
         k_vordiv_combine<float><<<p->T + 1, 256, 0, s>>>((float *)sout, (const float *)sout2, p->srow, p->T, Cp,
                                                          nfields);
+    ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

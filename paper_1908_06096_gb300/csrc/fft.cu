@@ -211,6 +211,7 @@ st_status launch_fb_tf32split(st_plan *p, int nfields, cudaStream_t s)
     const dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((C + 31) / 32));
     k_fb_tf32split<<<grid, 256, 0, s>>>((const float *)p->fb, (float *)p->fbop, rows, C, Cp, rows,
                                        rows * (long long)Cp);
+    ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

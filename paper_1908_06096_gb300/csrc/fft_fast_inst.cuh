@@ -70,6 +70,7 @@ st_status FF_LAUNCH(const FftJob *jobs, int n, cudaStream_t s)
     if (smem > 48 * 1024)
         ST_CUDA(cudaFuncSetAttribute(ff::FF_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     ff::FF_KERNEL<<<(unsigned)tot, ff::NT, smem, s>>>(B);
+    ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

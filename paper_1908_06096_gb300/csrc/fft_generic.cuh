@@ -957,6 +957,7 @@ inline st_status run_fft_batch(K kern, int threads, const FftJob *jobs, int n, s
     st_status r = set_smem(kern, smem);
     if (r) return r;
     kern<<<(unsigned)tot, threads, smem, s>>>(B);
+    ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

@@ -111,6 +111,7 @@ static st_status run_simt_batch(K kern, const SimtJob *jobs, const long long *bl
     if (tot == 0) return ST_OK;
     if (tot > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
     kern<<<(unsigned)tot, 256, 0, s>>>(B);
+    ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }
@@ -206,6 +207,7 @@ static st_status run_pack_batch(K kern, const PackJob *jobs, int n, cudaStream_t
     B.prefix[n] = tot;
     if (tot == 0) return ST_OK;
     kern<<<(unsigned)tot, 256, 0, s>>>(B);
+    ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;
 }

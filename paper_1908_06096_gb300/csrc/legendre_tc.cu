@@ -154,10 +154,12 @@ static st_status run_tc_batch(int prec, const TcJob *jobs, int n, int sm_count, 
         auto k = tc::k_leg_tc<0, MAXJ>;
         ST_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, tc::THREADS, smem, s>>>(B);
+        ++kernel_launches();
     } else {
         auto k = tc::k_leg_tc<1, MAXJ>;
         ST_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k<<<grid, tc::THREADS, smem, s>>>(B);
+        ++kernel_launches();
     }
     ST_CUDA(cudaGetLastError());
     return ST_OK;

@@ -459,6 +459,11 @@ st_status pers_launch(PersState *ps, cudaStream_t s);
 void pers_free(PersState *ps);
 size_t tc_smem_bytes(int prec, int max_nt, int *stages_out, size_t cap = 0);
 
+// ---- kernel launch count of the calling thread (api.cu): every launcher of
+// a transform kernel adds its launches, so that a plan's per-kind counters
+// report kernels, not calls.
+int &kernel_launches();
+
 // ---- plan helpers (api.cu) ----
 st_status count_launch(st_plan *p, int kind, cudaStream_t s, const std::function<st_status()> &f);
 st_status plan_alloc(st_plan *p, void **ptr, size_t bytes);
