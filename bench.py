@@ -342,7 +342,9 @@ def run_ours(args, ws, rank, local):
     total_k = sum(v["total_ms"] for v in ktimes.values()) or 1.0
     for name, v in ktimes.items():
         per = v["total_ms"] / max(v["timed"], 1)
-        e = {"launches": v["launches"], "ms_per_launch": per, "share": v["total_ms"] / total_k}
+        # launches: kernels; calls: stage calls timed (ms_per_launch is per call)
+        e = {"launches": v["launches"], "calls": v["timed"], "ms_per_launch": per,
+             "share": v["total_ms"] / total_k}
         if name.startswith("legendre") and prec in ("bf16x3", "tf32x3"):
             e.update(bound="tensor", unit="TFLOP/s", achieved=alg["leg_tensor_flops"] / (per * 1e-3) / 1e12,
                      peak=tensor_peak)

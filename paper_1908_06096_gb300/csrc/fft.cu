@@ -65,7 +65,10 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
     base.err = p->err;
 
     // fast rows
-    const size_t budget = (size_t)(kb > 0 ? kb : p->fft_kb[dir]) * 1024;
+    // launch variant 1 of the direct transform runs 512-thread CTAs: twice
+    // the budget of a 256-thread CTA, within one SM's shared memory
+    size_t budget = (size_t)(kb > 0 ? kb : p->fft_kb[dir]) * 1024;
+    if (kb <= 0 && dir == 1 && p->fft_var[1] == 1) budget = std::min<size_t>(2 * budget, 216 * 1024);
     for (int r = 0; r < p->nfast;) {
         const RowPair &rp = p->rowpairs_h[p->row_order[r]];
         const int id = rp.fast;
@@ -129,7 +132,6 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
 st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s, int variant)
 {
     if (n <= 0) return ST_OK;
-    (void)variant;
     for (int kind = -1; kind < FF_NGROUPS; ++kind) {
         std::vector<FftJob> sel;
         for (int q = 0; q < n; ++q)
@@ -147,7 +149,7 @@ st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t s
                     r = prec == P_FP64 ? launch_gen_inv_f64(sel.data() + i, m, need, s)
                                        : launch_gen_inv_f32(sel.data() + i, m, need, s);
             } else {
-                r = launch_fftf(dir, kind, sel.data() + i, m, s);
+                r = launch_fftf(dir, kind, sel.data() + i, m, s, variant);
             }
             if (r) return r;
         }
@@ -156,8 +158,16 @@ st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t s
     return ST_OK;
 }
 
-st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_t s)
+st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_t s, int variant)
 {
+    if (dir == 1 && variant == 1) {
+        switch (group) {
+        case 0: return launch_fftf_dirw_g0(jobs, n, s);
+        case 1: return launch_fftf_dirw_g1(jobs, n, s);
+        case 2: return launch_fftf_dirw_g2(jobs, n, s);
+        }
+        return ST_ERR_ARG;
+    }
     switch (dir * 4 + group) {
     case 0: return launch_fftf_inv_g0(jobs, n, s);
     case 1: return launch_fftf_inv_g1(jobs, n, s);

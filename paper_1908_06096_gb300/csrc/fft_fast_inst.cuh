@@ -9,7 +9,7 @@
 #endif
 
 namespace st {
-namespace ff {
+namespace FF_NS {
 
 // Plans outside this translation unit's group are never instantiated here.
 template <int GRP, class PL>
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(NT, MINB) FF_KERNEL(const __grid_constant__ Ff
     }
 }
 
-}  // namespace ff
+}  // namespace FF_NS
 
 st_status FF_LAUNCH(const FftJob *jobs, int n, cudaStream_t s)
 {
@@ -68,8 +68,8 @@ st_status FF_LAUNCH(const FftJob *jobs, int n, cudaStream_t s)
     if (tot > 0x7fffffffLL) return ST_ERR_UNSUPPORTED;
     if (smem > 227 * 1024) return ST_ERR_UNSUPPORTED;
     if (smem > 48 * 1024)
-        ST_CUDA(cudaFuncSetAttribute(ff::FF_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    ff::FF_KERNEL<<<(unsigned)tot, ff::NT, smem, s>>>(B);
+        ST_CUDA(cudaFuncSetAttribute(FF_NS::FF_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    FF_NS::FF_KERNEL<<<(unsigned)tot, FF_NS::NT, smem, s>>>(B);
     ++kernel_launches();
     ST_CUDA(cudaGetLastError());
     return ST_OK;

@@ -409,7 +409,10 @@ st_status launch_fb_tf32split(st_plan *p, int nfields, cudaStream_t s);
 st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t smem, cudaStream_t s,
                           int variant = 0);
 // fast-kernel launch of n jobs of one group (all jobs' kind == group), one direction
-st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_t s, int variant = 0);
+st_status launch_fftf_dirw_g0(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_dirw_g1(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_dirw_g2(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dir_g0(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dir_g1(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dir_g2(const FftJob *jobs, int n, cudaStream_t s);
