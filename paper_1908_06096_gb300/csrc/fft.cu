@@ -65,10 +65,10 @@ st_status fft_jobs(st_plan *p, int dir, int nfields, const void *src, void *dst,
     base.err = p->err;
 
     // fast rows
-    // launch variant 1 of the direct transform runs 512-thread CTAs: twice
-    // the budget of a 256-thread CTA, within one SM's shared memory
+    // launch variant 1 runs 512-thread CTAs: twice the budget of a
+    // 256-thread CTA, within one SM's shared memory
     size_t budget = (size_t)(kb > 0 ? kb : p->fft_kb[dir]) * 1024;
-    if (kb <= 0 && dir == 1 && p->fft_var[1] == 1) budget = std::min<size_t>(2 * budget, 216 * 1024);
+    if (kb <= 0 && p->prec != P_FP64 && p->fft_var[dir] == 1) budget = std::min<size_t>(2 * budget, 216 * 1024);
     for (int r = 0; r < p->nfast;) {
         const RowPair &rp = p->rowpairs_h[p->row_order[r]];
         const int id = rp.fast;
@@ -160,11 +160,14 @@ st_status launch_fft_jobs(int dir, int prec, const FftJob *jobs, int n, size_t s
 
 st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_t s, int variant)
 {
-    if (dir == 1 && variant == 1) {
-        switch (group) {
-        case 0: return launch_fftf_dirw_g0(jobs, n, s);
-        case 1: return launch_fftf_dirw_g1(jobs, n, s);
-        case 2: return launch_fftf_dirw_g2(jobs, n, s);
+    if (variant == 1) {
+        switch (dir * 4 + group) {
+        case 0: return launch_fftf_invw_g0(jobs, n, s);
+        case 1: return launch_fftf_invw_g1(jobs, n, s);
+        case 2: return launch_fftf_invw_g2(jobs, n, s);
+        case 4: return launch_fftf_dirw_g0(jobs, n, s);
+        case 5: return launch_fftf_dirw_g1(jobs, n, s);
+        case 6: return launch_fftf_dirw_g2(jobs, n, s);
         }
         return ST_ERR_ARG;
     }

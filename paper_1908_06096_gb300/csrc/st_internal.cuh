@@ -413,6 +413,9 @@ st_status launch_fftf(int dir, int group, const FftJob *jobs, int n, cudaStream_
 st_status launch_fftf_dirw_g0(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dirw_g1(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dirw_g2(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_invw_g0(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_invw_g1(const FftJob *jobs, int n, cudaStream_t s);
+st_status launch_fftf_invw_g2(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dir_g0(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dir_g1(const FftJob *jobs, int n, cudaStream_t s);
 st_status launch_fftf_dir_g2(const FftJob *jobs, int n, cudaStream_t s);

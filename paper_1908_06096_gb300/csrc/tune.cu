@@ -1,8 +1,8 @@
 // Autotuner (st_plan_autotune): times candidate launch shapes on the plan
 // itself and keeps the fastest.
 //  - FFT, per direction: the shared-memory budget per CTA, which sets how
-//    many fields a CTA holds (FP32 plans), and for the direct transform the
-//    CTA width (256 threads, or 512 with twice the budget).
+//    many fields a CTA holds (FP32 plans), and the CTA width (256 threads,
+//    or 512 with twice the budget).
 //  - Tensor-core Legendre: the inverse column-tile width (the tile shape of
 //    the per-m GEMMs; changing it re-lays out the tables), first for all m,
 //    then for the upper half of the wavenumbers alone (their reductions are
@@ -55,8 +55,8 @@ extern "C" st_status st_plan_autotune(st_plan_t p, int nfields, const char *cach
     // FFT launch shapes, per direction
     // (FP64 plans size their CTAs by a fixed budget: nothing to choose)
     const int kbs[] = {36, 54, 72, 108, 144};
-    // FP32 direct: variant 1 runs 512-thread CTAs (twice the fields a CTA)
-    const int nvar_dir = p->prec == P_FP64 ? 0 : 2, nvar_inv = p->prec == P_FP64 ? 0 : 1;
+    // FP32: variant 1 runs 512-thread CTAs (twice the fields a CTA)
+    const int nvar_dir = p->prec == P_FP64 ? 0 : 2, nvar_inv = nvar_dir;
     for (int dir = 0; dir < 2 && r == ST_OK; ++dir) {
         float best = 1e30f;
         int bv = p->fft_var[dir], bk = p->fft_kb[dir];
