@@ -795,8 +795,13 @@ st_status st_plan_create(st_plan_t *out, int T, const st_grid_desc *grid, int pr
     p->nlon = grid->kind == ST_GRID_REGULAR ? grid->nlon : 0;
     p->prec = prec;
     p->max_fields = max_fields;
-    // fast kernels: two CTAs of 256 threads per SM (128 registers a thread)
-    if (prec != ST_FP64) p->fft_kb[0] = p->fft_kb[1] = 108;
+    // fast kernels: two CTAs of 256 threads per SM (128 registers a thread);
+    // the direct transform in 512-thread CTAs with twice the budget (the
+    // autotuner's choice at T639 and T1279)
+    if (prec != ST_FP64) {
+        p->fft_kb[0] = p->fft_kb[1] = 108;
+        p->fft_var[1] = 1;
+    }
     cudaError_t e = cudaGetDevice(&p->device);
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e, "cudaGetDevice"); }
     cudaDeviceProp prop;
