@@ -36,6 +36,7 @@ WORKLOADS = {
     "t159_reg_411": (159, "regular", 160, 320, 411, 1.0, 1001),
     "t639_o640_64": (639, "octahedral", 1280, 0, 64, 1.5, 1002),
     "t639_o640_256": (639, "octahedral", 1280, 0, 256, 1.5, 1002),
+    "t639_o640_128": (639, "octahedral", 1280, 0, 128, 1.5, 1002),
     "t31_reg_10": (31, "regular", 32, 64, 10, 1.0, 1000),
     # the operational resolution of the paper's test cases: TCO1279 on O1280
     # (2560 Gaussian latitudes, rows 20 + 4i up to 5140 points), 137 levels
@@ -267,6 +268,7 @@ def config_of(wl, prec):
             "t159_reg_411": "T159 regular 160 x 320 Gaussian grid, 137 levels x 3 fields",
             "t639_o640_64": "T639 octahedral O640, 64 fields (profiling case)",
             "t639_o640_256": "T639 octahedral O640, 256 fields (profiling case of the Legendre GEMM)",
+            "t639_o640_128": "T639 octahedral O640, 128 fields (profiling case of the Legendre GEMM, ~3 GB)",
             "t31_reg_10": "T31 regular 32 x 64 Gaussian grid, 10 fields",
             "t1279_o1280_137": "T1279 octahedral O1280 (2560 Gaussian latitudes, rows 20+4i), 137 levels x 1 field"}[wl]
     return {"workload": desc, "T": T, "grid": grid, "nlat": nlat, "nlon": nlon or None, "fields": F,
