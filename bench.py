@@ -56,33 +56,81 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+def parse_clock_lines(lines, t0=None, t1=None):
+    """Median SM clock, maximum clock and active throttle reasons of the
+    nvidia-smi samples (CLOCK_FIELDS, csv, no units) stamped inside the
+    window [t0, t1] (datetime; None: every sample)."""
+    import datetime
+    sm, smax, reasons = [], None, set()
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+        except ValueError:
+            ts = None
+        if ts is not None and ((t0 is not None and ts < t0) or (t1 is not None and ts > t1)):
+            continue
+        try:
+            sm.append(float(f[2]))
+            smax = float(f[3])
+        except ValueError:
+            continue
+        for n, v in zip(CLOCK_REASONS, f[6:10]):
+            if v.lower() == "active":
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 20 ms; start() before the
+    warm-up (the tool takes a while to produce its first sample), begin() and
+    end() around the timed region, whose samples alone stop() reports."""
 
     def __init__(self, device_index: int):
         self.idx = device_index
         self.proc = None
         self.lines = []
         self.thread = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+            import shutil
+            # line-buffered, so that no sample is still in the tool's buffer when it is stopped
+            pre = ["stdbuf", "-oL"] if shutil.which("stdbuf") else []
+            self.proc = subprocess.Popen(pre + ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={CLOCK_FIELDS}",
+                                                "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t < 5.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def begin(self):
+        import datetime
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        import datetime
+        time.sleep(0.05)  # the sample of the last timed step is printed after it
+        self.t1 = datetime.datetime.now()
 
     def stop(self):
         if self.proc is None:
@@ -94,22 +142,10 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = parse_clock_lines(self.lines, self.t0, self.t1)
+        if self.t0 is not None and self.t1 is not None:
+            out["window_ms"] = round((self.t1 - self.t0).total_seconds() * 1e3, 1)
+        return out
 
 
 def geometry(rows, T):
@@ -308,21 +344,23 @@ def run_ours(args, ws, rank, local):
         plan.inv(spec, out=g)
         plan.dir(g, out=s_out)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(args.warmup):
         step()
     plan.sync()
     plan.reset_timings()
     plan.set_timing(True)
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.begin()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     barrier(ws)
     ck = clocks.stop()
     plan.set_timing(False)
