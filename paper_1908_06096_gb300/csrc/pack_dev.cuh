@@ -57,60 +57,48 @@ __device__ __forceinline__ void pack_block(const PackJob &J, int b, Rr (*tile)[6
     const long long q0 = (long long)m * (T + 1) - (long long)m * (m - 1) / 2;
     const int len = T - m + 1;
     const long long rowE = J.srow[2 * m], rowO = J.srow[2 * m + 1];
+    // one vector load per complex value where the caller's spectra allow it
+    // (every value then starts at a multiple of its own size)
+    using V2 = std::conditional_t<std::is_same<Rr, double>::value, double2, float2>;
+    const bool vec = (reinterpret_cast<uintptr_t>(spec) & (sizeof(V2) - 1)) == 0;
     for (int d0 = 0; d0 < len; d0 += 32 * CH) {
-        if constexpr (CH == 1 && NW == 8) {
-            // a full 256-thread block: load and stage field by field (its
-            // neighbours on the SM hide the latency)
-            for (int ff = warp; ff < 32; ff += 8) {
-                const int fld = f0 + ff, d = d0 + lane;
-                Rr re = 0, im = 0;
+        // load: warp w reads fields w, w + NW, ... of each chunk (all loads
+        // in flight before the first store); lane = d
+        constexpr int FK = 32 / NW;
+        Rr re[CH][FK], im[CH][FK];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+            for (int k = 0; k < FK; ++k) {
+                const int fld = f0 + warp + NW * k, d = d0 + 32 * c + lane;
+                re[c][k] = im[c][k] = 0;
                 if (fld < nfields && d < len) {
                     const Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
-                    re = a[0];
-                    im = m == 0 ? (Rr)0 : a[1];
+                    if (vec) {
+                        const V2 z = *reinterpret_cast<const V2 *>(a);
+                        re[c][k] = z.x;
+                        im[c][k] = z.y;
+                    } else {
+                        re[c][k] = a[0];
+                        im[c][k] = a[1];
+                    }
+                    if (m == 0) im[c][k] = 0;
                     if (J.scale) {
                         // inverse Laplacian on the unit sphere: -1 / (n (n+1)), 0 at n = 0
                         const int n = m + d;
                         const Rr f = n == 0 ? (Rr)0 : (Rr)(-1.0 / ((double)n * (n + 1.0)));
-                        re *= f;
-                        im *= f;
+                        re[c][k] *= f;
+                        im[c][k] *= f;
                     }
                 }
-                tile[lane][2 * ff] = re;
-                tile[lane][2 * ff + 1] = im;
             }
-        } else {
-            // load: warp w reads fields w, w + NW, ... of each chunk (all loads
-            // in flight before the first store); lane = d
-            constexpr int FK = 32 / NW;
-            Rr re[CH][FK], im[CH][FK];
 #pragma unroll
-            for (int c = 0; c < CH; ++c)
+        for (int c = 0; c < CH; ++c)
 #pragma unroll
-                for (int k = 0; k < FK; ++k) {
-                    const int fld = f0 + warp + NW * k, d = d0 + 32 * c + lane;
-                    re[c][k] = im[c][k] = 0;
-                    if (fld < nfields && d < len) {
-                        const Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
-                        re[c][k] = a[0];
-                        im[c][k] = m == 0 ? (Rr)0 : a[1];
-                        if (J.scale) {
-                            // inverse Laplacian on the unit sphere: -1 / (n (n+1)), 0 at n = 0
-                            const int n = m + d;
-                            const Rr f = n == 0 ? (Rr)0 : (Rr)(-1.0 / ((double)n * (n + 1.0)));
-                            re[c][k] *= f;
-                            im[c][k] *= f;
-                        }
-                    }
-                }
-#pragma unroll
-            for (int c = 0; c < CH; ++c)
-#pragma unroll
-                for (int k = 0; k < FK; ++k) {
-                    tile[32 * c + lane][2 * (warp + NW * k)] = re[c][k];
-                    tile[32 * c + lane][2 * (warp + NW * k) + 1] = im[c][k];
-                }
-        }
+            for (int k = 0; k < FK; ++k) {
+                tile[32 * c + lane][2 * (warp + NW * k)] = re[c][k];
+                tile[32 * c + lane][2 * (warp + NW * k) + 1] = im[c][k];
+            }
         sync();
         if constexpr (S == S_TF32_SPLIT) {
             // column-major operand (rows contiguous per column): warp w
@@ -156,6 +144,9 @@ __device__ __forceinline__ void unpack_block(const PackJob &J, int b, Rr (*tile)
     const int len = T - m + 1;
     const long long rowE = J.srow[2 * m], rowO = J.srow[2 * m + 1];
     const bool zero = m > J.max_m;
+    // one vector store per complex value where the caller's spectra allow it
+    using V2 = std::conditional_t<std::is_same<Rr, double>::value, double2, float2>;
+    const bool vec = (reinterpret_cast<uintptr_t>(spec) & (sizeof(V2) - 1)) == 0;
     for (int d0 = 0; d0 < len; d0 += 32 * CH) {
         // rows d = w, w+8, ... of each chunk; all loads in flight first
         constexpr int DK = 32 / NW;
@@ -187,8 +178,17 @@ __device__ __forceinline__ void unpack_block(const PackJob &J, int b, Rr (*tile)
                 const int d = d0 + 32 * c + lane;
                 if (fld < nfields && d < len) {
                     Rr *a = spec + ((long long)fld * nspec + q0 + d) * 2;
-                    a[0] = tile[32 * c + lane][2 * ff];
-                    a[1] = m == 0 ? (Rr)0 : tile[32 * c + lane][2 * ff + 1];
+                    const Rr re = tile[32 * c + lane][2 * ff];
+                    const Rr im = m == 0 ? (Rr)0 : tile[32 * c + lane][2 * ff + 1];
+                    if (vec) {
+                        V2 z;
+                        z.x = re;
+                        z.y = im;
+                        *reinterpret_cast<V2 *>(a) = z;
+                    } else {
+                        a[0] = re;
+                        a[1] = im;
+                    }
                 }
             }
         }

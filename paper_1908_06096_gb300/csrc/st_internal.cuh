@@ -388,7 +388,7 @@ inline long long fb_rows(const st_plan *p) { return 2LL * (p->T + 1) * p->Jp; }
 inline long long fb_row(const st_plan *p, int par, int m, int j) { return ((long long)par * (p->T + 1) + m) * p->Jp + j; }
 // Row pitch (columns) of the packed operands and the Fourier buffer for
 // 2 nfields data columns: a multiple of 8 (16-byte rows in the bf16 planes),
-// and from 512 columns on a multiple of 64, so that every row of every plane
+// and from 256 columns on a multiple of 64, so that every row of every plane
 // starts on a 128-byte line.  Rows that start inside a 32-byte sector leave
 // partly written sectors behind the GEMM epilogue and the pack stores: at
 // T639 O640, 548 fields (1096 columns) ran the Legendre kernels 7-9 % slower
@@ -398,7 +398,7 @@ inline long long fb_row(const st_plan *p, int par, int m, int j) { return ((long
 inline int cols_padded(int nfields)
 {
     const int C = 2 * nfields;
-    return C < 512 ? ((C + 7) / 8) * 8 : ((C + 63) / 64) * 64;
+    return C < 256 ? ((C + 7) / 8) * 8 : ((C + 63) / 64) * 64;
 }
 
 // Tensor-core Legendre kernel geometry: 128 data columns per tile; a reduction
