@@ -259,7 +259,7 @@ def oracle_round_trip(T, grid, nlat, nlon, spec):
     return time.perf_counter() - t0, oracle.max_threads()
 
 
-def cpu_baseline(wl, sample_fields=8):
+def cpu_baseline(wl, sample_fields=24):
     from paper_1908_06096_gb300 import inputs
     T, grid, nlat, nlon, F, p, seed = WORKLOADS[wl]
     n = min(sample_fields, F)
@@ -717,7 +717,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32", "fp64"])
     ap.add_argument("--skip-forms", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-fields", type=int, default=8)
+    ap.add_argument("--cpu-fields", type=int, default=24)
     ap.add_argument("--ref-fields", type=int, default=2)
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
