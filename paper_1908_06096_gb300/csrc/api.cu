@@ -188,6 +188,13 @@ static void plan_free(st_plan *p)
     delete p;
 }
 
+// Widest table column tile of the direct GEMMs: 160 is the widest at which
+// three pipeline stages (2 x 128 x 128 B of data operand + 2 x 160 x 128 B of
+// table a stage) fit in shared memory; with 256 (two stages) the direct GEMMs
+// ran 9 % slower at T639 O640 x 548 and 7 % at T1279 O1280 x 137, with 128
+// (more tiles, the data operand re-read) 3 % slower.
+constexpr int TC_NT_DIR = 160;
+
 // Group layout for one direction and precision (see LegGroup).
 static void build_groups(st_plan *p, int dir)
 {
@@ -245,8 +252,10 @@ static void build_groups(st_plan *p, int dir)
                     g.nt = m < m_split ? nt_inv : nt_hi;
                     g.nct = m < m_split ? nct_inv : nct_hi;
                 } else {
+                    // direct column tiles: the table columns are the K_m
+                    // degrees of (m, parity), the fewest tiles of <= TC_NT_DIR
                     int n = std::max(g.ncol, 1);
-                    g.nct = (n + 255) / 256;
+                    g.nct = (n + TC_NT_DIR - 1) / TC_NT_DIR;
                     g.nt = ((n + g.nct - 1) / g.nct + 15) / 16 * 16;
                 }
                 g.nkc = (std::max(g.K, 1) + kc - 1) / kc;

@@ -20,7 +20,9 @@ namespace st {
 namespace {
 
 constexpr char kMagic[8] = {'S', 'T', 'T', 'A', 'B', 'L', 'E', 'S'};
-constexpr uint32_t kVersion = 1;
+// 2: the direct tables' column tiles are at most 160 columns wide (files of
+// format 1 hold the 256-wide layout and are rebuilt)
+constexpr uint32_t kVersion = 2;
 
 struct Header {
     char magic[8];
