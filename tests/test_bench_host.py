@@ -1,8 +1,11 @@
-"""Host-side logic of bench.py that needs no GPU: the clock record.
+"""Host-side logic of bench.py that needs no GPU: the clock record and the
+FFT flop model's plan lengths.
 
 The benchmark reports the median SM clock and the throttle reasons that
 nvidia-smi saw during the timed region; samples stamped outside that window
-(start-up, warm-up, the copy-out afterwards) must not count.
+(start-up, warm-up, the copy-out afterwards) must not count.  Its FFT flop
+count follows the lengths the library's compile-time plans run, so its copy
+of those lengths must match the library's plan table.
 """
 import datetime
 import os
@@ -43,3 +46,19 @@ def test_clock_record_flags_throttle_reasons_in_the_window():
 def test_clock_record_without_tool():
     s = bench.ClockSampler(0)
     assert s.stop()["samples"] == 0
+
+
+def test_flop_model_uses_the_library_plan_lengths():
+    """bench.FF_LENGTHS (the FFT flop model) lists exactly the lengths of the
+    compile-time plans in the library's ST_FF_PLANS table."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1908_06096_gb300", "csrc", "st_internal.cuh")).read()
+    table = src[src.index("#define ST_FF_PLANS(X)"):]
+    table = table[:table.index("constexpr int FF_NPLANS")]
+    lengths = set()
+    for m in re.finditer(r"X\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\)", table):
+        a, b, c, d = (int(m.group(i)) for i in range(3, 7))
+        lengths.add(a * b * c * d)
+    n = int(re.search(r"constexpr int FF_NPLANS = (\d+);", src).group(1))
+    assert len(re.findall(r"X\(\d+,", table)) == n
+    assert sorted(lengths) == sorted(bench.FF_LENGTHS)
